@@ -1,0 +1,9 @@
+"""CPU oracle of the CHNS hot path (plain FP64 numpy / PyTorch CPU).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU-baseline
+and reference legs of the benchmark may import it; the library never does.
+"""
+from .mesh import Mesh
+from .chns import Oracle, Params, basis_tables
+
+__all__ = ["Mesh", "Oracle", "Params", "basis_tables"]

@@ -1,0 +1,135 @@
+"""Oracle mesh: independent nodes and hanging-node constraints of a 2:1-balanced
+octree (Section 4, "Handling hanging nodes").
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import this package.
+
+Conventions (shared with the CUDA path only through the documented C-ABI
+behaviour, never through code):
+  * Leaves are ``(x, y, z, level)`` integer anchors in units of the finest cell,
+    sorted in Morton order; the domain is the cube [lo, hi]^d.
+  * Element corner ``a`` (0 <= a < 2^d) sits at anchor + size * bit_k(a) along
+    axis k (x is bit 0).
+  * A corner is *hanging* when it lies at the midpoint of an edge (one "odd" axis)
+    or the centre of a face (two "odd" axes, 3D) of a leaf one level coarser.  Its
+    value is then the mean of the 2 (edge) or 4 (face) corners of that edge or face:
+    the Q1 interpolant of the coarse side, which keeps the field continuous.
+  * Independent nodes are all non-hanging corner points, numbered in Morton order of
+    their integer coordinates (max_level + 1 bits per axis).
+  * Boundary nodes are those with some coordinate equal to 0 or 2^max_level.
+"""
+import numpy as np
+
+
+def _morton(coords, bits):
+    coords = np.asarray(coords, dtype=np.int64)
+    n, d = coords.shape
+    key = np.zeros(n, dtype=np.int64)
+    for b in range(bits):
+        for k in range(d):
+            key |= ((coords[:, k] >> b) & 1) << (b * d + k)
+    return key
+
+
+class Mesh:
+    """Plain numpy description of the finite-element mesh of a leaf list."""
+
+    def __init__(self, dim, max_level, leaves, lo=0.0, hi=1.0):
+        leaves = np.asarray(leaves, dtype=np.int64)
+        self.dim = d = int(dim)
+        self.max_level = L = int(max_level)
+        self.lo, self.hi = float(lo), float(hi)
+        self.nc = nc = 1 << d
+        self.nf = d + 3
+        anchors = leaves[:, :d]
+        level = leaves[:, 3]
+        size = np.int64(1) << (L - level)
+        self.E = E = leaves.shape[0]
+        self.anchors, self.level, self.size = anchors, level, size
+        self.h = (self.hi - self.lo) * (0.5 ** level.astype(np.float64))
+
+        bits = np.array([[(a >> k) & 1 for k in range(d)] for a in range(nc)], dtype=np.int64)
+        corners = anchors[:, None, :] + bits[None, :, :] * size[:, None, None]  # (E, nc, d)
+        cflat = corners.reshape(-1, d)
+        sflat = np.repeat(size, nc)
+        lflat = np.repeat(level, nc)
+
+        # leaf lookup: key of (anchor, level)
+        leaf_key = np.sort(_morton(anchors, L) * 64 + level)
+
+        def is_leaf(anc, lev):
+            k = _morton(anc, L) * 64 + lev
+            i = np.searchsorted(leaf_key, k)
+            i = np.minimum(i, leaf_key.shape[0] - 1)
+            return leaf_key[i] == k
+
+        odd = ((cflat // sflat[:, None]) & 1) == 1          # axes where the corner is mid-way
+        nodd = odd.sum(axis=1)
+        n_side = np.int64(1) << L
+        hanging = np.zeros(cflat.shape[0], dtype=bool)
+        cand = np.nonzero((nodd >= 1) & (nodd <= 2) & (nodd < d) & (lflat > 0))[0]
+        if cand.size:
+            c = cflat[cand]
+            s = sflat[cand]
+            o = odd[cand]
+            nfree = d - nodd[cand]
+            free_rank = np.cumsum(~o, axis=1) - 1          # rank of each non-odd axis
+            # coarse leaves (size 2s) holding c on an edge/face: anchor = c - s on odd
+            # axes, c - 2s or c on the other axes
+            found = np.zeros(cand.size, dtype=bool)
+            for combo in range(1 << (d - 1)):
+                shift = ((combo >> np.maximum(free_rank, 0)) & 1).astype(bool) & ~o
+                anc = np.where(o, c - s[:, None], np.where(shift, c - 2 * s[:, None], c))
+                valid = (combo < (1 << nfree)) & np.all((anc >= 0) & (anc < n_side), axis=1)
+                if np.any(valid):
+                    idx = np.nonzero(valid)[0]
+                    found[idx] |= is_leaf(anc[idx], lflat[cand][idx] - 1)
+            hanging[cand[found]] = True
+
+        # independent nodes: every non-hanging corner point
+        nb = L + 1
+        indep = cflat[~hanging]
+        keys = np.unique(_morton(indep, nb))
+        self.N = N = keys.shape[0]
+        # decode node coordinates from keys
+        nodes = np.zeros((N, d), dtype=np.int64)
+        for b in range(nb):
+            for k in range(d):
+                nodes[:, k] |= ((keys >> (b * d + k)) & 1) << b
+        self.nodes = nodes
+        self.x = self.lo + (self.hi - self.lo) * nodes.astype(np.float64) / float(n_side)
+        self.boundary = np.any((nodes == 0) | (nodes == n_side), axis=1)
+
+        def node_index(pts):
+            k = _morton(pts, nb)
+            i = np.searchsorted(keys, k)
+            i = np.minimum(i, N - 1)
+            if not np.all(keys[i] == k):
+                raise ValueError("constraint parent is not an independent node (mesh not 2:1 balanced)")
+            return i
+
+        parents = np.zeros((cflat.shape[0], 4), dtype=np.int64)
+        weights = np.zeros((cflat.shape[0], 4), dtype=np.float64)
+        nh = ~hanging
+        parents[nh, 0] = node_index(cflat[nh])
+        weights[nh, 0] = 1.0
+        hi_idx = np.nonzero(hanging)[0]
+        if hi_idx.size:
+            c = cflat[hi_idx]
+            s = sflat[hi_idx]
+            o = odd[hi_idx]
+            no = nodd[hi_idx]
+            odd_rank = np.cumsum(o, axis=1) - 1
+            for m in range(4):
+                use = m < (1 << no)
+                if not np.any(use):
+                    continue
+                up = ((m >> np.maximum(odd_rank, 0)) & 1).astype(bool)
+                p = np.where(o, np.where(up, c + s[:, None], c - s[:, None]), c)
+                sel = hi_idx[use]
+                parents[sel, m] = node_index(p[use])
+                weights[sel, m] = 1.0 / (1 << no[use])
+        self.parents = parents.reshape(E, nc, 4)
+        self.weights = weights.reshape(E, nc, 4)
+        self.hanging = hanging.reshape(E, nc)
+        # physical corner coordinates (E, nc, d)
+        self.corner_x = self.lo + (self.hi - self.lo) * corners.astype(np.float64) / float(n_side)
