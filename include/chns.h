@@ -1,0 +1,169 @@
+/*
+ * chns.h -- C-ABI of the GB300 matrix-free CHNS hot path.
+ *
+ * Method: the fully-coupled, Crank-Nicolson, variational-multiscale (RBVMS)
+ * Cahn-Hilliard Navier-Stokes scheme of Khanwale et al. (arXiv 2009.06628):
+ * time scheme and weak form of Definition 1 (Section 3), the fully discrete VMS
+ * form of Definition 2 with its stabilisation parameters and strong residuals
+ * (Section 3.3), Newton's method of Section 3.4, on Q1 elements of a 2:1
+ * balanced octree with hanging nodes (Section 4).
+ *
+ * Conventions shared by every call:
+ *  - dim d in {2, 3}; n_f = d + 3 fields per node in the order v_1..v_d, p, phi, mu.
+ *  - Vectors are caller-owned, contiguous, node-major and interleaved:
+ *    U[node * n_f + field].  Pointers documented "device" must be CUDA device
+ *    pointers (e.g. torch CUDA tensors); "host" pointers are ordinary memory.
+ *  - Independent nodes are numbered in Morton (Z) order of their integer
+ *    coordinates (units of the finest cell, max_level + 1 bits per axis, x fastest).
+ *  - Dirichlet rows: every velocity component of every node on the boundary of
+ *    the domain cube has the row R = v^{k+1} (no-slip, Definition 1).  If
+ *    params.pin_pressure != 0 the pressure row of node 0 (the corner at lo^d) is
+ *    R = p^{k+1} - p^k, which fixes the constant left free by closed no-slip boxes.
+ *  - Calls that take a `stream` (a cudaStream_t passed as void*, NULL = legacy
+ *    default stream) are asynchronous on it, unless they return host scalars
+ *    (mass, energy, Newton statistics, mu0), which synchronise that stream.
+ *  - A mesh holds device workspace; one mesh may be used by one stream at a time.
+ *  - On any error nothing of the caller's outputs is written before validation
+ *    fails; a status other than CHNS_OK is returned and chns_last_error() gives
+ *    a message (thread-local).
+ */
+#ifndef CHNS_H
+#define CHNS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CHNS_OK = 0,
+    CHNS_EINVAL = 1,          /* bad argument (null pointer, dim, level, size, precision) */
+    CHNS_ENOTSORTED = 2,      /* leaves not strictly increasing in Morton order */
+    CHNS_ENOTCOMPLETE = 3,    /* leaves overlap, leave gaps, or are misaligned */
+    CHNS_ENOTBALANCED = 4,    /* two leaves sharing a point differ by more than one level */
+    CHNS_ENOMEM = 5,          /* host or device allocation failed */
+    CHNS_ECUDA = 6,           /* a CUDA runtime call failed */
+    CHNS_ENAN = 7,            /* a non-finite norm appeared in Newton/Krylov */
+    CHNS_ENOCONV = 8,         /* Newton did not reach the tolerance within max_newton */
+    CHNS_EBREAKDOWN = 9,      /* Krylov breakdown (zero or non-finite Arnoldi vector) */
+    CHNS_ETAU = 10            /* a stabilisation radicand was not positive */
+} chns_status;
+
+/* Opaque mesh: immutable after creation, owns its device arrays and workspace. */
+typedef struct chns_mesh chns_mesh;
+
+/* One octree leaf: integer anchor in units of the finest cell (2^max_level cells
+ * per axis; z = 0 in 2D) and its level.  16 bytes, matching an (n, 4) int32 array. */
+typedef struct {
+    int32_t x, y, z, level;
+} chns_leaf;
+
+/* Physical and numerical parameters of one time step (Section 2 groups).
+ * rho_+ = eta_+ = 1 belong to the phi = +1 phase; rho_- = 1/rho_ratio,
+ * eta_- = 1/eta_ratio (Eq. alpha_beta_defn).  Fr <= 0 disables gravity; gravity
+ * points along -e_{d-1} (last axis).  C_I, C_phi: the constants of tau_m, tau_phi
+ * (6 in the paper).  dt: the time step (also the Delta t inside tau). */
+typedef struct {
+    int32_t dim;
+    int32_t pin_pressure;
+    double Re, We, Pe, Cn, Fr;
+    double rho_ratio, eta_ratio;
+    double dt;
+    double C_I, C_phi;
+} chns_params;
+
+/* Newton-Krylov options.  precision: 0 = FP64 everywhere; 1 = FP32 J.x and
+ * preconditioner inside the Krylov solver, FP64 residual, orthogonalisation, dots,
+ * norms and update (Newton acts as iterative refinement).  Newton stops when
+ * ||R||_2 <= rtol * ||R(U^0)||_2 or ||R||_2 <= atol.  Krylov: right-preconditioned
+ * GMRES(restart) with nodal block-Jacobi, relative tolerance krylov_rtol, at most
+ * max_krylov iterations per Newton iteration. */
+typedef struct {
+    double rtol, atol, krylov_rtol;
+    int32_t max_newton, max_krylov, restart, precision;
+} chns_solver_opts;
+
+/* Statistics of one Newton step (filled also on CHNS_ENOCONV / ENAN / EBREAKDOWN). */
+typedef struct {
+    int32_t newton_its, krylov_its, jvp_calls, reason;
+    double res0, res_final, du_norm;
+} chns_stats;
+
+/* Build a mesh from a Morton-sorted, complete, 2:1 balanced leaf list (Section 4:
+ * octant-to-node map, hanging-node virtualisation).  leaves: host array of n_leaves.
+ * Domain: the cube [lo, hi]^dim.  Validates sortedness, completeness, alignment and
+ * full (face/edge/vertex) 2:1 balance; enumerates independent nodes, element-to-
+ * node map, hanging-node constraints (edge mid-point: 1/2 of 2 parents; face
+ * centre: 1/4 of 4 parents) and the boundary nodes, then copies them to the
+ * current CUDA device.  *out receives the mesh (library-owned; free with
+ * chns_mesh_destroy).  Limits: 1 <= max_level <= 20. */
+chns_status chns_mesh_create(int32_t dim, int32_t max_level, int64_t n_leaves,
+                             const chns_leaf* leaves, double lo, double hi, chns_mesh** out);
+
+/* Free a mesh and its device memory (NULL is ignored). */
+void chns_mesh_destroy(chns_mesh* mesh);
+
+int64_t chns_mesh_num_nodes(const chns_mesh* mesh);     /* independent nodes N */
+int64_t chns_mesh_num_elements(const chns_mesh* mesh);  /* leaves E */
+int64_t chns_mesh_num_hanging(const chns_mesh* mesh);   /* distinct hanging points */
+int32_t chns_mesh_dim(const chns_mesh* mesh);
+
+/* Copy the integer coordinates of the independent nodes (units of the finest
+ * cell) to host memory coords[N * dim]. */
+chns_status chns_mesh_node_coords(const chns_mesh* mesh, int32_t* coords);
+
+/* Residual R(U^k, U^{k+1}) of Definition 2 with the Crank-Nicolson substitution of
+ * Definition 1 (Section 3.3 end), FP64.  U_old = U^k, U_new = U^{k+1}, R: device
+ * arrays of N * n_f doubles.  R is overwritten.  A non-positive tau radicand
+ * produces non-finite entries (reported as CHNS_ETAU by chns_newton_step). */
+chns_status chns_residual(const chns_mesh* mesh, const chns_params* params,
+                          const double* U_old, const double* U_new, double* R, void* stream);
+
+/* Newton Jacobian-vector product y = J x, J = dR/dU^{k+1} evaluated at
+ * U^{k+1} = U_lin (Eq. newton_linear_system; analytic variations, Section 3.4),
+ * computed by forward-mode differentiation of the element map.  precision 0: all
+ * four arrays are double; precision 1: all four are float (FP32 arithmetic).
+ * Dirichlet and pin rows of J are identity rows (y = x there).  y is overwritten. */
+chns_status chns_jvp(const chns_mesh* mesh, const chns_params* params, const void* U_old,
+                     const void* U_lin, const void* x, void* y, int32_t precision, void* stream);
+
+/* Transpose product (reverse mode, FP64): gU_new = J^T w = w^T dR/dU^{k+1},
+ * gU_old = w^T dR/dU^k, *gCn = w^T dR/dCn (a single device double), evaluated at
+ * (U_old, U_lin).  All outputs are overwritten.  Any of gU_old / gCn may be NULL. */
+chns_status chns_vjp(const chns_mesh* mesh, const chns_params* params, const double* U_old,
+                     const double* U_lin, const double* w, double* gU_new, double* gU_old,
+                     double* gCn, void* stream);
+
+/* One implicit time step (Section 3.4): solve R(U_old, U) = 0 by inexact Newton from
+ * U^{0} = U_old (U_inout is overwritten with U_old first) with matrix-free GMRES.
+ * U_old, U_inout: device, N * n_f doubles.  stats: host, may be NULL.  Synchronises
+ * the stream.  The first call on a mesh allocates the Krylov workspace. */
+chns_status chns_newton_step(const chns_mesh* mesh, const chns_params* params,
+                             const chns_solver_opts* opts, const double* U_old, double* U_inout,
+                             chns_stats* stats, void* stream);
+
+/* Integral of phi over the domain (mass, Proposition 1), FP64, to host *out. */
+chns_status chns_mass(const chns_mesh* mesh, const double* U, double* out, void* stream);
+
+/* Parts of E_tot (Eq. energy_functional) at one time level, FP64, to host out[3]:
+ * out[0] = 1/2 int rho(phi*) |v|^2, out[1] = 1/(Cn We) int psi(phi) + Cn^2/2 |grad phi|^2,
+ * out[2] = 1/Fr int rho(phi*) x_{d-1} (0 without gravity). */
+chns_status chns_energy(const chns_mesh* mesh, const chns_params* params, const double* U,
+                        double* out, void* stream);
+
+/* Consistent initial chemical potential: overwrite the mu field of U_inout (device)
+ * with the solution of M mu = (N, psi'(phi)) + Cn^2 (grad N, grad phi), the potential
+ * equation at one time level (Definition 1), by Jacobi-preconditioned CG to a
+ * relative residual of 1e-14.  Synchronises the stream. */
+chns_status chns_initial_mu(const chns_mesh* mesh, const chns_params* params, double* U_inout,
+                            void* stream);
+
+/* Message of the last error on this thread ("" if none). */
+const char* chns_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHNS_H */

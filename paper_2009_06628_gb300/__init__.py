@@ -1,0 +1,220 @@
+"""Thin Python binding of libchns (the C-ABI declared in include/chns.h).
+
+Only argument marshalling happens here: torch tensors supply device memory and the
+current CUDA stream; every step of the hot path runs in the library's CUDA kernels.
+The binding refuses to work without the compiled library (there is no CPU path).
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+__all__ = ["lib", "load", "Params", "SolverOpts", "Stats", "ChnsError", "Mesh", "residual", "jvp", "vjp",
+           "newton_step", "mass", "energy", "initial_mu", "LIB_PATH"]
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libchns.so")
+
+STATUS = {0: "CHNS_OK", 1: "CHNS_EINVAL", 2: "CHNS_ENOTSORTED", 3: "CHNS_ENOTCOMPLETE", 4: "CHNS_ENOTBALANCED",
+          5: "CHNS_ENOMEM", 6: "CHNS_ECUDA", 7: "CHNS_ENAN", 8: "CHNS_ENOCONV", 9: "CHNS_EBREAKDOWN",
+          10: "CHNS_ETAU"}
+
+
+class ChnsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = STATUS.get(code, str(code))
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("pin_pressure", ctypes.c_int32), ("Re", ctypes.c_double),
+                ("We", ctypes.c_double), ("Pe", ctypes.c_double), ("Cn", ctypes.c_double), ("Fr", ctypes.c_double),
+                ("rho_ratio", ctypes.c_double), ("eta_ratio", ctypes.c_double), ("dt", ctypes.c_double),
+                ("C_I", ctypes.c_double), ("C_phi", ctypes.c_double)]
+
+    @classmethod
+    def make(cls, dim, Re, We, Pe, Cn, Fr, rho_ratio, eta_ratio, dt, C_I=6.0, C_phi=6.0, pin_pressure=1,
+             **_ignored):
+        return cls(dim=dim, pin_pressure=pin_pressure, Re=Re, We=We, Pe=Pe, Cn=Cn, Fr=Fr, rho_ratio=rho_ratio,
+                   eta_ratio=eta_ratio, dt=dt, C_I=C_I, C_phi=C_phi)
+
+
+class SolverOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("atol", ctypes.c_double), ("krylov_rtol", ctypes.c_double),
+                ("max_newton", ctypes.c_int32), ("max_krylov", ctypes.c_int32), ("restart", ctypes.c_int32),
+                ("precision", ctypes.c_int32)]
+
+    @classmethod
+    def make(cls, rtol=1e-9, atol=1e-14, krylov_rtol=1e-3, max_newton=20, max_krylov=2000, restart=60,
+             precision=1):
+        return cls(rtol=rtol, atol=atol, krylov_rtol=krylov_rtol, max_newton=max_newton, max_krylov=max_krylov,
+                   restart=restart, precision=precision)
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("newton_its", ctypes.c_int32), ("krylov_its", ctypes.c_int32), ("jvp_calls", ctypes.c_int32),
+                ("reason", ctypes.c_int32), ("res0", ctypes.c_double), ("res_final", ctypes.c_double),
+                ("du_norm", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+# (name, restype, argtypes) of every entry point in include/chns.h
+P = ctypes.c_void_p
+SIGNATURES = [
+    ("chns_mesh_create", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, P, ctypes.c_double,
+                                        ctypes.c_double, ctypes.POINTER(ctypes.c_void_p)]),
+    ("chns_mesh_destroy", None, [P]),
+    ("chns_mesh_num_nodes", ctypes.c_int64, [P]),
+    ("chns_mesh_num_elements", ctypes.c_int64, [P]),
+    ("chns_mesh_num_hanging", ctypes.c_int64, [P]),
+    ("chns_mesh_dim", ctypes.c_int32, [P]),
+    ("chns_mesh_node_coords", ctypes.c_int, [P, P]),
+    ("chns_residual", ctypes.c_int, [P, P, P, P, P, P]),
+    ("chns_jvp", ctypes.c_int, [P, P, P, P, P, P, ctypes.c_int32, P]),
+    ("chns_vjp", ctypes.c_int, [P, P, P, P, P, P, P, P, P]),
+    ("chns_newton_step", ctypes.c_int, [P, P, P, P, P, P, P]),
+    ("chns_mass", ctypes.c_int, [P, P, P, P]),
+    ("chns_energy", ctypes.c_int, [P, P, P, P, P]),
+    ("chns_initial_mu", ctypes.c_int, [P, P, P, P]),
+    ("chns_last_error", ctypes.c_char_p, []),
+]
+
+
+def load(path=None):
+    """Load libchns.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"libchns.so not found at {path}: run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def lib():
+    return load()
+
+
+def _check(code):
+    if code != 0:
+        raise ChnsError(code, load().chns_last_error().decode())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t, dtype=torch.float64):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"expected a contiguous {dtype} CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Mesh:
+    """Owns a chns_mesh built from an (n, 4) int32 leaf array (x, y, z, level)."""
+
+    def __init__(self, dim, max_level, leaves, lo=0.0, hi=1.0):
+        L = load()
+        leaves = np.ascontiguousarray(np.asarray(leaves, dtype=np.int32))
+        if leaves.ndim != 2 or leaves.shape[1] != 4:
+            raise ValueError("leaves must be an (n, 4) int32 array")
+        h = ctypes.c_void_p()
+        _check(L.chns_mesh_create(int(dim), int(max_level), int(leaves.shape[0]),
+                                  leaves.ctypes.data_as(ctypes.c_void_p), float(lo), float(hi), ctypes.byref(h)))
+        self._h = h
+        self.dim = int(dim)
+        self.nf = self.dim + 3
+        self.max_level = int(max_level)
+        self.lo, self.hi = float(lo), float(hi)
+        self.N = int(L.chns_mesh_num_nodes(h))
+        self.E = int(L.chns_mesh_num_elements(h))
+        self.H = int(L.chns_mesh_num_hanging(h))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def node_coords(self):
+        out = np.zeros((self.N, self.dim), dtype=np.int32)
+        _check(load().chns_mesh_node_coords(self._h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def node_x(self):
+        return self.lo + (self.hi - self.lo) * self.node_coords().astype(np.float64) / float(1 << self.max_level)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().chns_mesh_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def residual(mesh, prm, U_old, U_new, out=None):
+    out = torch.empty_like(U_new) if out is None else out
+    _check(load().chns_residual(mesh.handle, ctypes.byref(prm), _ptr(U_old), _ptr(U_new), _ptr(out), _stream()))
+    return out
+
+
+def jvp(mesh, prm, U_old, U_lin, x, out=None):
+    """y = J(U_lin) x in the dtype of the inputs (float64 or float32)."""
+    dt = x.dtype
+    prec = {torch.float64: 0, torch.float32: 1}[dt]
+    out = torch.empty_like(x) if out is None else out
+    _check(load().chns_jvp(mesh.handle, ctypes.byref(prm), _ptr(U_old, dt), _ptr(U_lin, dt), _ptr(x, dt),
+                           _ptr(out, dt), prec, _stream()))
+    return out
+
+
+def vjp(mesh, prm, U_old, U_lin, w, want_old=True, want_cn=True):
+    gn = torch.empty_like(w)
+    go = torch.empty_like(w) if want_old else None
+    gc = torch.empty(1, dtype=torch.float64, device=w.device) if want_cn else None
+    _check(load().chns_vjp(mesh.handle, ctypes.byref(prm), _ptr(U_old), _ptr(U_lin), _ptr(w), _ptr(gn),
+                           _ptr(go) if go is not None else None, _ptr(gc) if gc is not None else None, _stream()))
+    return gn, go, gc
+
+
+def newton_step(mesh, prm, opts, U_old, U_out=None, check=True):
+    U_out = torch.empty_like(U_old) if U_out is None else U_out
+    st = Stats()
+    code = load().chns_newton_step(mesh.handle, ctypes.byref(prm), ctypes.byref(opts), _ptr(U_old), _ptr(U_out),
+                                   ctypes.byref(st), _stream())
+    if check:
+        _check(code)
+    return U_out, st
+
+
+def mass(mesh, U):
+    out = ctypes.c_double()
+    _check(load().chns_mass(mesh.handle, _ptr(U), ctypes.byref(out), _stream()))
+    return out.value
+
+
+def energy(mesh, prm, U):
+    out = (ctypes.c_double * 3)()
+    _check(load().chns_energy(mesh.handle, ctypes.byref(prm), _ptr(U), out, _stream()))
+    return tuple(out)
+
+
+def initial_mu(mesh, prm, U):
+    """Overwrite the mu field of U (in place) with the discrete mu^0 of its phi."""
+    _check(load().chns_initial_mu(mesh.handle, ctypes.byref(prm), _ptr(U), _stream()))
+    return U

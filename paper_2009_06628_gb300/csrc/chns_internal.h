@@ -1,0 +1,88 @@
+// Internal declarations shared by the translation units of libchns.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "chns.h"
+
+// Everything a kernel needs to know about the mesh (plain pointers into device memory).
+struct DevMesh {
+    int32_t dim, nc, nf;
+    int64_t E, N, H, NB;
+    const int32_t* e2n;     // E * nc: >= 0 independent node, < 0: -(hanging index + 1)
+    const int32_t* hang;    // H * 4 parent node indices; -1 marks an unused slot (edge case)
+    const int8_t* level;    // E element levels
+    const uint8_t* nflag;   // N node flags, bit 0: on the domain boundary
+    const int32_t* bnodes;  // NB boundary node indices
+    const int32_t* anchor;  // E * dim element anchors (units of the finest cell)
+    int32_t max_level;
+    double lo, hi;
+};
+
+struct SolverWS;  // Newton-Krylov workspace (solver.cu)
+
+struct chns_mesh {
+    DevMesh dm;
+    int32_t max_level;
+    std::vector<int32_t> node_coords;  // host copy, N * dim
+    // owning device pointers
+    int32_t* d_e2n = nullptr;
+    int32_t* d_hang = nullptr;
+    int8_t* d_level = nullptr;
+    uint8_t* d_nflag = nullptr;
+    int32_t* d_bnodes = nullptr;
+    int32_t* d_anchor = nullptr;
+    // reduction workspace: per-block partial sums and a flag word
+    double* d_partials = nullptr;
+    int64_t n_partials = 0;
+    double* h_pinned = nullptr;      // pinned host landing zone for scalar results
+    unsigned int* d_flags = nullptr; // bit 0: a tau radicand was not positive
+    SolverWS* ws = nullptr;
+};
+
+// Kernel-side parameter block derived from chns_params (all FP64; kernels cast).
+struct PhysConst {
+    double dt, inv_dt, four_over_dt2;
+    double inv_Re, inv_We, inv_Pe, inv_Fr;  // inv_Fr = 0: no gravity
+    double Cn, We, Pe, Re;
+    double rho_plus, rho_minus;
+    double alpha, beta, gamma, xi;
+    double C_I, C_phi;
+};
+
+// error helpers (capi.cpp)
+void chns_set_error(const std::string& msg);
+chns_status chns_cuda_status(cudaError_t err, const char* where);
+chns_status chns_check_params(const chns_mesh* mesh, const chns_params* p, PhysConst* out);
+
+#define CHNS_CUDA(call)                                                   \
+    do {                                                                  \
+        cudaError_t e_ = (call);                                          \
+        if (e_ != cudaSuccess) return chns_cuda_status(e_, #call);        \
+    } while (0)
+
+// kernel launchers (element_kernels.cu, reduce_kernels.cu)
+cudaError_t launch_residual(const chns_mesh* m, const PhysConst& pc, const double* U_old,
+                            const double* U_new, double* R, int pin, cudaStream_t s);
+cudaError_t launch_jvp64(const chns_mesh* m, const PhysConst& pc, const double* U_old,
+                         const double* U_lin, const double* x, double* y, int pin, cudaStream_t s);
+cudaError_t launch_jvp32(const chns_mesh* m, const PhysConst& pc, const float* U_old,
+                         const float* U_lin, const float* x, float* y, int pin, cudaStream_t s);
+cudaError_t launch_vjp(const chns_mesh* m, const PhysConst& pc, const double* U_old,
+                       const double* U_lin, const double* w, double* gU_new, double* gU_old,
+                       double* gCn, int pin, cudaStream_t s);
+cudaError_t launch_mass(const chns_mesh* m, const double* U, double* out_dev, cudaStream_t s);
+cudaError_t launch_energy(const chns_mesh* m, const PhysConst& pc, const double* U,
+                          double* out_dev3, cudaStream_t s);
+// deterministic FP64 reductions into device scalars (solver.cu uses them)
+cudaError_t launch_dot(const chns_mesh* m, const double* a, const double* b, int64_t n, double* out_dev,
+                       cudaStream_t s);
+cudaError_t launch_multidot(const chns_mesh* m, const double* V, int64_t ld, int k, const double* w, int64_t n,
+                            double* out_dev, cudaStream_t s);
+
+// grid sizing helper: SM count of the current device (cached)
+int chns_num_sms();

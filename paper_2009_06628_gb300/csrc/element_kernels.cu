@@ -1,0 +1,676 @@
+// Element kernels of the matrix-free hot path: residual (FP64), J x (FP64 / FP32,
+// forward mode through Dual numbers) and J^T w (FP64, reverse mode).
+//
+// Thread mapping: 2^d threads per element; during the gather thread t owns element
+// corner t, during the physics it owns Gauss point t, during the test contraction
+// it owns corner t again.  An element's threads sit in one warp, so the exchanges go
+// through shared memory with __syncwarp.  Elements are processed in their Morton
+// order (consecutive elements share most nodes, which keeps gathers in L2/L1).
+//
+// Hanging corners (Section 4): a corner value is the mean of its 2 (edge) or 4 (face)
+// parent nodes; the scatter applies the transpose (the same weights).
+#include <cuda_runtime.h>
+
+#include "chns_internal.h"
+#include "pointwise.cuh"
+
+namespace {
+
+template <int D>
+struct Shape {
+    static constexpr int NC = 1 << D;      // corners = Gauss points
+    static constexpr int NF = D + 3;       // fields
+    static constexpr int NH = (D == 2) ? 1 : 3;
+    static constexpr int EPB = (D == 2) ? 32 : 16;  // elements per 128-thread block
+};
+
+template <class T> struct GaussC;
+template <> struct GaussC<double> {
+    static constexpr double cp = 0.78867513459481288225;  // (1 + 1/sqrt 3)/2
+    static constexpr double cm = 0.21132486540518711775;  // (1 - 1/sqrt 3)/2
+};
+template <> struct GaussC<float> {
+    static constexpr float cp = 0.78867513459481288225f;
+    static constexpr float cm = 0.21132486540518711775f;
+};
+
+// Q1 basis of corner a at Gauss point q (both as bit patterns), physical derivatives.
+template <int D, class T>
+struct Basis {
+    T N, dN[D], d2N[Shape<D>::NH];
+};
+
+template <int D, class T>
+__device__ __forceinline__ Basis<D, T> basis(int a, int q, T inv_h) {
+    T f[D], s[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const bool same = ((a >> k) & 1) == ((q >> k) & 1);
+        f[k] = same ? GaussC<T>::cp : GaussC<T>::cm;
+        s[k] = ((a >> k) & 1) ? inv_h : -inv_h;
+    }
+    Basis<D, T> b;
+    if constexpr (D == 2) {
+        b.N = f[0] * f[1];
+        b.dN[0] = s[0] * f[1];
+        b.dN[1] = f[0] * s[1];
+        b.d2N[0] = s[0] * s[1];
+    } else {
+        b.N = f[0] * f[1] * f[D - 1];
+        b.dN[0] = s[0] * f[1] * f[D - 1];
+        b.dN[1] = f[0] * s[1] * f[D - 1];
+        b.dN[D - 1] = f[0] * f[1] * s[D - 1];
+        b.d2N[0] = s[0] * s[1] * f[D - 1];
+        b.d2N[1 % Shape<D>::NH] = s[0] * f[1] * s[D - 1];
+        b.d2N[2 % Shape<D>::NH] = f[0] * s[1] * s[D - 1];
+    }
+    return b;
+}
+
+template <class T>
+__device__ __forceinline__ T clip1(T x) { return x > T(1) ? T(1) : (x < T(-1) ? T(-1) : x); }
+
+template <class T>
+__device__ __forceinline__ T phys_h(const DevMesh& m, int lev) {
+    return T(ldexp(m.hi - m.lo, -lev));
+}
+
+// Corner parents and weights of element corner entry `ent`.
+struct Parents {
+    int n;
+    int p[4];
+};
+
+__device__ __forceinline__ Parents parents_of(const DevMesh& m, int ent) {
+    Parents P;
+    if (ent >= 0) {
+        P.n = 1;
+        P.p[0] = ent;
+        P.p[1] = P.p[2] = P.p[3] = 0;
+    } else {
+        const int4 hp = reinterpret_cast<const int4*>(m.hang)[-ent - 1];
+        P.p[0] = hp.x;
+        P.p[1] = hp.y;
+        P.p[2] = hp.z < 0 ? 0 : hp.z;
+        P.p[3] = hp.w < 0 ? 0 : hp.w;
+        P.n = hp.z < 0 ? 2 : 4;
+    }
+    return P;
+}
+
+// Primal corner data of one element in shared memory.
+template <int D, class T>
+struct CornerPrimal {
+    T ut[Shape<D>::NC][Shape<D>::NF];   // mid-point average
+    T dd[Shape<D>::NC][D + 1];          // (new - old) for v and phi
+    T ps[Shape<D>::NC];                 // phi* (clip at independent nodes, interpolated)
+};
+
+// Gather of corner `a`: averages, differences and phi*; returns the clip masks of the
+// parents (bit j set: parent j has |phi~| <= 1) for the tangent / adjoint.
+template <int D, class T>
+__device__ __forceinline__ unsigned gather_primal(const DevMesh& m, const Parents& P, const T* __restrict__ Uo,
+                                                  const T* __restrict__ Un, CornerPrimal<D, T>& C, int a) {
+    constexpr int NF = Shape<D>::NF;
+    T so[NF], sn[NF];
+    T ps = T(0);
+    unsigned mask = 0;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) so[f] = sn[f] = T(0);
+    const T w = (P.n == 1) ? T(1) : (P.n == 2 ? T(0.5) : T(0.25));
+    for (int j = 0; j < P.n; ++j) {
+        const T* po = Uo + (size_t)P.p[j] * NF;
+        const T* pn = Un + (size_t)P.p[j] * NF;
+        T o[NF], n[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            o[f] = __ldg(po + f);
+            n[f] = __ldg(pn + f);
+            so[f] += w * o[f];
+            sn[f] += w * n[f];
+        }
+        const T avg = T(0.5) * (o[D + 1] + n[D + 1]);
+        if (avg <= T(1) && avg >= T(-1)) mask |= 1u << j;
+        ps += w * clip1(avg);
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) C.ut[a][f] = T(0.5) * (so[f] + sn[f]);
+#pragma unroll
+    for (int i = 0; i < D; ++i) C.dd[a][i] = sn[i] - so[i];
+    C.dd[a][D] = sn[D + 1] - so[D + 1];
+    C.ps[a] = ps;
+    return mask;
+}
+
+// Interpolate the primal quadrature-point inputs at Gauss point q.
+template <int D, class T>
+__device__ __forceinline__ void interp_primal(const CornerPrimal<D, T>& C, int q, T inv_h, T inv_dt,
+                                              QPIn<D, T>& X) {
+    constexpr int NC = Shape<D>::NC;
+    X.p = X.phi = X.mu = X.phidt = X.divnew = X.ps = T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        X.v[k] = X.gp[k] = X.gphi[k] = X.gmu[k] = X.vdt[k] = X.gps[k] = T(0);
+#pragma unroll
+        for (int j = 0; j < D; ++j) X.gv[k][j] = T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < Shape<D>::NH; ++k) X.H[k] = T(0);
+#pragma unroll
+    for (int a = 0; a < NC; ++a) {
+        const Basis<D, T> b = basis<D, T>(a, q, inv_h);
+        const T* u = C.ut[a];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            X.v[i] += b.N * u[i];
+#pragma unroll
+            for (int k = 0; k < D; ++k) X.gv[i][k] += b.dN[k] * u[i];
+            X.vdt[i] += b.N * C.dd[a][i];
+            X.divnew += b.dN[i] * (u[i] + T(0.5) * C.dd[a][i]);
+        }
+        X.p += b.N * u[D];
+        X.phi += b.N * u[D + 1];
+        X.mu += b.N * u[D + 2];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            X.gp[k] += b.dN[k] * u[D];
+            X.gphi[k] += b.dN[k] * u[D + 1];
+            X.gmu[k] += b.dN[k] * u[D + 2];
+            X.gps[k] += b.dN[k] * C.ps[a];
+        }
+#pragma unroll
+        for (int k = 0; k < Shape<D>::NH; ++k) X.H[k] += b.d2N[k] * u[D + 1];
+        X.phidt += b.N * C.dd[a][D];
+        X.ps += b.N * C.ps[a];
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) X.vdt[i] *= inv_dt;
+    X.phidt *= inv_dt;
+}
+
+template <class R>
+__host__ __device__ PCst<R> make_pcst(const PhysConst& pc) {
+    PCst<R> c;
+    c.alpha = R(pc.alpha);
+    c.beta = R(pc.beta);
+    c.gamma = R(pc.gamma);
+    c.xi = R(pc.xi);
+    c.Jc = R((pc.rho_minus - pc.rho_plus) / (2.0 * pc.rho_plus * pc.Cn));
+    c.inv_Pe = R(pc.inv_Pe);
+    c.inv_We = R(pc.inv_We);
+    c.inv_Re = R(pc.inv_Re);
+    c.inv_Fr = R(pc.inv_Fr);
+    c.Cn_We = R(pc.Cn * pc.inv_We);
+    c.inv_PeCn = R(1.0 / (pc.Pe * pc.Cn));
+    c.Cn2 = R(pc.Cn * pc.Cn);
+    c.Pe = R(pc.Pe);
+    c.Re = R(pc.Re);
+    c.four_over_dt2 = R(pc.four_over_dt2);
+    c.C_I = R(pc.C_I);
+    c.C_phi = R(pc.C_phi);
+    return c;
+}
+
+// Test-function contraction for corner a from the per-Gauss-point fluxes in shared
+// memory (already scaled by |det J| w_q): r[f] = sum_q N_a f0 + grad N_a . f1.
+template <int D, class T>
+__device__ __forceinline__ void contract(const T (*sf)[Shape<D>::NF * (D + 1)], int a, T inv_h,
+                                         T r[Shape<D>::NF]) {
+    constexpr int NF = Shape<D>::NF;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) r[f] = T(0);
+#pragma unroll
+    for (int q = 0; q < Shape<D>::NC; ++q) {
+        const Basis<D, T> b = basis<D, T>(a, q, inv_h);
+        const T* s = sf[q];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            T acc = b.N * s[f];
+#pragma unroll
+            for (int k = 0; k < D; ++k) acc += b.dN[k] * s[NF + f * D + k];
+            r[f] += acc;
+        }
+    }
+}
+
+template <int D, class T>
+__device__ __forceinline__ void scatter_add(T* __restrict__ out, const Parents& P, const T r[Shape<D>::NF]) {
+    constexpr int NF = Shape<D>::NF;
+    const T w = (P.n == 1) ? T(1) : (P.n == 2 ? T(0.5) : T(0.25));
+    for (int j = 0; j < P.n; ++j) {
+        T* o = out + (size_t)P.p[j] * NF;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) atomicAdd(o + f, w * r[f]);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Residual (MODE_RES) and J x (MODE_JVP) share one kernel body.
+// ---------------------------------------------------------------------------------
+enum { MODE_RES = 0, MODE_JVP = 1 };
+
+template <int D, class T, int MODE>
+struct SmemRJ {
+    CornerPrimal<D, T> cp;
+    T x[MODE == MODE_JVP ? Shape<D>::NC : 1][Shape<D>::NF];   // tangent corner values
+    T xps[MODE == MODE_JVP ? Shape<D>::NC : 1];               // tangent of phi*
+    T f[Shape<D>::NC][Shape<D>::NF * (D + 1)];                // fluxes per Gauss point
+};
+
+template <int D, class T, int MODE>
+__global__ void __launch_bounds__(128) elem_rj_kernel(DevMesh m, PCst<T> c, T inv_dt,
+                                                      const T* __restrict__ Uo,
+                                                      const T* __restrict__ Un,
+                                                      const T* __restrict__ xin, T* __restrict__ out,
+                                                      unsigned int* __restrict__ flags) {
+    constexpr int NC = Shape<D>::NC, NF = Shape<D>::NF, EPB = Shape<D>::EPB;
+    __shared__ SmemRJ<D, T, MODE> sm[EPB];
+    const int le = threadIdx.x / NC;
+    const int t = threadIdx.x % NC;
+    const int64_t e = (int64_t)blockIdx.x * EPB + le;
+    const bool valid = e < m.E;
+    SmemRJ<D, T, MODE>& S = sm[le];
+
+    Parents P;
+    P.n = 0;
+    T inv_h = T(1), detJ = T(0);
+    if (valid) {
+        const int ent = m.e2n[e * NC + t];
+        P = parents_of(m, ent);
+        const unsigned mask = gather_primal<D, T>(m, P, Uo, Un, S.cp, t);
+        const T h = phys_h<T>(m, m.level[e]);
+        inv_h = T(1) / h;
+        detJ = (D == 2) ? (T(0.25) * h * h) : (T(0.125) * h * h * h);
+        if (MODE == MODE_JVP) {
+            T sx[NF];
+            T xps = T(0);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) sx[f] = T(0);
+            const T w = (P.n == 1) ? T(1) : (P.n == 2 ? T(0.5) : T(0.25));
+            for (int j = 0; j < P.n; ++j) {
+                const T* px = xin + (size_t)P.p[j] * NF;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) sx[f] += w * __ldg(px + f);
+                if (mask & (1u << j)) xps += w * T(0.5) * __ldg(px + D + 1);
+            }
+#pragma unroll
+            for (int f = 0; f < NF; ++f) S.x[t][f] = sx[f];
+            S.xps[t] = xps;
+        }
+    }
+    __syncwarp();
+    if (valid) {
+        const int q = t;
+        const T g = T(4) * inv_h * inv_h;
+        QPIn<D, T> X;
+        interp_primal<D, T>(S.cp, q, inv_h, inv_dt, X);
+        if (MODE == MODE_RES) {
+            QPOut<D, T> F;
+            pointwise<D, T, T>(X, c, g, F);
+            // non-positive tau_m radicand shows up as a non-finite tau
+            if (!(F.f1[D][0] == F.f1[D][0])) atomicOr(flags, 1u);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                S.f[q][f] = detJ * F.f0[f];
+#pragma unroll
+                for (int k = 0; k < D; ++k) S.f[q][NF + f * D + k] = detJ * F.f1[f][k];
+            }
+        } else {
+            // tangent inputs: averages move by x/2, differences by x
+            QPIn<D, Dual<T>> XD;
+            T xv[NF], xg[NF][D], xH[Shape<D>::NH], xdiv = T(0), xpsv = T(0), xpsg[D];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                xv[f] = T(0);
+#pragma unroll
+                for (int k = 0; k < D; ++k) xg[f][k] = T(0);
+            }
+#pragma unroll
+            for (int k = 0; k < Shape<D>::NH; ++k) xH[k] = T(0);
+#pragma unroll
+            for (int k = 0; k < D; ++k) xpsg[k] = T(0);
+#pragma unroll
+            for (int a = 0; a < NC; ++a) {
+                const Basis<D, T> b = basis<D, T>(a, q, inv_h);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    const T u = S.x[a][f];
+                    xv[f] += b.N * u;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) xg[f][k] += b.dN[k] * u;
+                }
+#pragma unroll
+                for (int k = 0; k < Shape<D>::NH; ++k) xH[k] += b.d2N[k] * S.x[a][D + 1];
+                xpsv += b.N * S.xps[a];
+#pragma unroll
+                for (int k = 0; k < D; ++k) xpsg[k] += b.dN[k] * S.xps[a];
+            }
+#pragma unroll
+            for (int i = 0; i < D; ++i) xdiv += xg[i][i];
+            const T hf = T(0.5);
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                XD.v[i] = Dual<T>(X.v[i], hf * xv[i]);
+#pragma unroll
+                for (int k = 0; k < D; ++k) XD.gv[i][k] = Dual<T>(X.gv[i][k], hf * xg[i][k]);
+                XD.vdt[i] = Dual<T>(X.vdt[i], inv_dt * xv[i]);
+                XD.gp[i] = Dual<T>(X.gp[i], hf * xg[D][i]);
+                XD.gphi[i] = Dual<T>(X.gphi[i], hf * xg[D + 1][i]);
+                XD.gmu[i] = Dual<T>(X.gmu[i], hf * xg[D + 2][i]);
+                XD.gps[i] = Dual<T>(X.gps[i], xpsg[i]);
+            }
+            XD.p = Dual<T>(X.p, hf * xv[D]);
+            XD.phi = Dual<T>(X.phi, hf * xv[D + 1]);
+            XD.mu = Dual<T>(X.mu, hf * xv[D + 2]);
+#pragma unroll
+            for (int k = 0; k < Shape<D>::NH; ++k) XD.H[k] = Dual<T>(X.H[k], hf * xH[k]);
+            XD.phidt = Dual<T>(X.phidt, inv_dt * xv[D + 1]);
+            XD.divnew = Dual<T>(X.divnew, xdiv);
+            XD.ps = Dual<T>(X.ps, xpsv);
+            QPOut<D, Dual<T>> F;
+            pointwise<D, Dual<T>, T>(XD, c, g, F);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                S.f[q][f] = detJ * F.f0[f].d;
+#pragma unroll
+                for (int k = 0; k < D; ++k) S.f[q][NF + f * D + k] = detJ * F.f1[f][k].d;
+            }
+        }
+    }
+    __syncwarp();
+    if (valid) {
+        T r[NF];
+        contract<D, T>(S.f, t, inv_h, r);
+        scatter_add<D, T>(out, P, r);
+    }
+}
+
+// Dirichlet (no-slip) rows and the pressure pin.
+//   residual: R = v^{k+1} on boundary velocity rows; R[0,p] = p^{k+1} - p^k
+//   J x     : y = x on those rows
+template <int D, class T>
+__global__ void bc_rows_kernel(DevMesh m, const T* __restrict__ a, const T* __restrict__ b,
+                               T* __restrict__ out, int pin) {
+    constexpr int NF = Shape<D>::NF;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m.NB) {
+        const int64_t n = m.bnodes[i];
+#pragma unroll
+        for (int k = 0; k < D; ++k) out[n * NF + k] = a[n * NF + k];
+    }
+    if (i == 0 && pin) out[D] = b ? (a[D] - b[D]) : a[D];
+}
+
+// ---------------------------------------------------------------------------------
+// J^T w (reverse mode, FP64)
+// ---------------------------------------------------------------------------------
+template <int D>
+struct NXb {
+    // packed adjoint of QPIn: v, gv, p, gp, phi, gphi, H, mu, gmu, vdt, phidt, divnew, ps, gps
+    static constexpr int n = D + D * D + 1 + D + 1 + D + Shape<D>::NH + 1 + D + D + 1 + 1 + 1 + D;
+};
+
+template <int D>
+struct SmemVJP {
+    CornerPrimal<D, double> cp;
+    double wb[Shape<D>::NC][Shape<D>::NF];
+    double xb[Shape<D>::NC][NXb<D>::n];
+};
+
+template <int D>
+__global__ void __launch_bounds__(64) elem_vjp_kernel(DevMesh m, PCst<double> c, double Cn, double inv_dt,
+                                                      const double* __restrict__ Uo,
+                                                      const double* __restrict__ Un,
+                                                      const double* __restrict__ w, double* __restrict__ gn,
+                                                      double* __restrict__ go, double* __restrict__ gCn, int pin) {
+    constexpr int NC = Shape<D>::NC, NF = Shape<D>::NF, NH = Shape<D>::NH, EPB = 64 / NC;
+    __shared__ SmemVJP<D> sm[EPB];
+    const int le = threadIdx.x / NC;
+    const int t = threadIdx.x % NC;
+    const int64_t e = (int64_t)blockIdx.x * EPB + le;
+    const bool valid = e < m.E;
+    SmemVJP<D>& S = sm[le];
+    Parents P;
+    P.n = 0;
+    unsigned mask = 0;
+    double inv_h = 1.0, detJ = 0.0;
+    if (valid) {
+        P = parents_of(m, m.e2n[e * NC + t]);
+        mask = gather_primal<D, double>(m, P, Uo, Un, S.cp, t);
+        const double h = phys_h<double>(m, m.level[e]);
+        inv_h = 1.0 / h;
+        detJ = (D == 2) ? 0.25 * h * h : 0.125 * h * h * h;
+        // adjoint seed: w on rows that the element contributes to (Dirichlet and pin
+        // rows are replaced rows, their element contributions are discarded)
+        double sw[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) sw[f] = 0.0;
+        const double wt = (P.n == 1) ? 1.0 : (P.n == 2 ? 0.5 : 0.25);
+        for (int j = 0; j < P.n; ++j) {
+            const int n = P.p[j];
+            const bool bnd = m.nflag[n] & 1;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                double wv = __ldg(w + (size_t)n * NF + f);
+                if (f < D && bnd) wv = 0.0;
+                if (f == D && pin && n == 0) wv = 0.0;
+                sw[f] += wt * wv;
+            }
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) S.wb[t][f] = sw[f];
+    }
+    __syncwarp();
+    double cnb = 0.0;
+    if (valid) {
+        const int q = t;
+        const double g = 4.0 * inv_h * inv_h;
+        QPIn<D, double> X;
+        interp_primal<D, double>(S.cp, q, inv_h, inv_dt, X);
+        QPOut<D, double> Fb;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            Fb.f0[f] = 0.0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) Fb.f1[f][k] = 0.0;
+        }
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+            const Basis<D, double> b = basis<D, double>(a, q, inv_h);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const double wv = detJ * S.wb[a][f];
+                Fb.f0[f] += b.N * wv;
+#pragma unroll
+                for (int k = 0; k < D; ++k) Fb.f1[f][k] += b.dN[k] * wv;
+            }
+        }
+        QPIn<D, double> Xb;
+        pointwise_adjoint<D>(X, c, Cn, g, Fb, Xb, cnb);
+        double* o = S.xb[q];
+        int k = 0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) o[k++] = Xb.v[i];
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) o[k++] = Xb.gv[i][j];
+        o[k++] = Xb.p;
+#pragma unroll
+        for (int i = 0; i < D; ++i) o[k++] = Xb.gp[i];
+        o[k++] = Xb.phi;
+#pragma unroll
+        for (int i = 0; i < D; ++i) o[k++] = Xb.gphi[i];
+#pragma unroll
+        for (int i = 0; i < NH; ++i) o[k++] = Xb.H[i];
+        o[k++] = Xb.mu;
+#pragma unroll
+        for (int i = 0; i < D; ++i) o[k++] = Xb.gmu[i];
+#pragma unroll
+        for (int i = 0; i < D; ++i) o[k++] = Xb.vdt[i];
+        o[k++] = Xb.phidt;
+        o[k++] = Xb.divnew;
+        o[k++] = Xb.ps;
+#pragma unroll
+        for (int i = 0; i < D; ++i) o[k++] = Xb.gps[i];
+    }
+    __syncwarp();
+    if (valid) {
+        // transpose of the interpolation for corner a = t
+        const int a = t;
+        double ut[NF], ddv[D + 1], divb[D], psb = 0.0;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) ut[f] = 0.0;
+#pragma unroll
+        for (int i = 0; i <= D; ++i) ddv[i] = 0.0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) divb[i] = 0.0;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+            const Basis<D, double> b = basis<D, double>(a, q, inv_h);
+            const double* x = S.xb[q];
+            int k = 0;
+#pragma unroll
+            for (int i = 0; i < D; ++i) ut[i] += b.N * x[k++];
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int j = 0; j < D; ++j) ut[i] += b.dN[j] * x[k++];
+            ut[D] += b.N * x[k++];
+#pragma unroll
+            for (int i = 0; i < D; ++i) ut[D] += b.dN[i] * x[k++];
+            ut[D + 1] += b.N * x[k++];
+#pragma unroll
+            for (int i = 0; i < D; ++i) ut[D + 1] += b.dN[i] * x[k++];
+#pragma unroll
+            for (int i = 0; i < NH; ++i) ut[D + 1] += b.d2N[i] * x[k++];
+            ut[D + 2] += b.N * x[k++];
+#pragma unroll
+            for (int i = 0; i < D; ++i) ut[D + 2] += b.dN[i] * x[k++];
+#pragma unroll
+            for (int i = 0; i < D; ++i) ddv[i] += b.N * x[k++];
+            ddv[D] += b.N * x[k++];
+            const double dvb = x[k++];
+#pragma unroll
+            for (int i = 0; i < D; ++i) divb[i] += b.dN[i] * dvb;
+            psb += b.N * x[k++];
+#pragma unroll
+            for (int i = 0; i < D; ++i) psb += b.dN[i] * x[k++];
+        }
+        // corner adjoints of U^{k+1} and U^k: averages take 1/2 each, differences +-1/dt,
+        // div v^{k+1} acts on the new level only
+        double rn[NF], ro[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) rn[f] = ro[f] = 0.5 * ut[f];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            rn[i] += inv_dt * ddv[i] + divb[i];
+            ro[i] -= inv_dt * ddv[i];
+        }
+        rn[D + 1] += inv_dt * ddv[D];
+        ro[D + 1] -= inv_dt * ddv[D];
+        const double wt = (P.n == 1) ? 1.0 : (P.n == 2 ? 0.5 : 0.25);
+        for (int j = 0; j < P.n; ++j) {
+            double* on = gn + (size_t)P.p[j] * NF;
+            double* oo = go ? go + (size_t)P.p[j] * NF : nullptr;
+            const double pst = (mask & (1u << j)) ? 0.5 * psb : 0.0;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const double extra = (f == D + 1) ? pst : 0.0;
+                atomicAdd(on + f, wt * (rn[f] + extra));
+                if (oo) atomicAdd(oo + f, wt * (ro[f] + extra));
+            }
+        }
+    }
+    if (gCn) {
+        // block reduction of d/dCn (each Gauss point thread holds its share)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) cnb += __shfl_xor_sync(0xffffffffu, cnb, off);
+        if ((threadIdx.x & 31) == 0 && cnb != 0.0) atomicAdd(gCn, cnb);
+    }
+}
+
+// Dirichlet/pin rows of J^T w: identity rows pass w through.
+template <int D>
+__global__ void bc_vjp_kernel(DevMesh m, const double* __restrict__ w, double* __restrict__ gn,
+                              double* __restrict__ go, int pin) {
+    constexpr int NF = Shape<D>::NF;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m.NB) {
+        const int64_t n = m.bnodes[i];
+#pragma unroll
+        for (int k = 0; k < D; ++k) gn[n * NF + k] += w[n * NF + k];
+    }
+    if (i == 0 && pin) {
+        gn[D] += w[D];
+        if (go) go[D] -= w[D];
+    }
+}
+
+template <int D, class T, int MODE>
+cudaError_t launch_rj(const chns_mesh* mm, const PhysConst& pc, const T* Uo, const T* Un, const T* x,
+                      T* out, int pin, cudaStream_t s) {
+    const DevMesh& m = mm->dm;
+    const size_t bytes = (size_t)m.N * Shape<D>::NF * sizeof(T);
+    cudaError_t err = cudaMemsetAsync(out, 0, bytes, s);
+    if (err != cudaSuccess) return err;
+    const int EPB = Shape<D>::EPB;
+    const int64_t blocks = (m.E + EPB - 1) / EPB;
+    elem_rj_kernel<D, T, MODE><<<(unsigned)blocks, EPB * Shape<D>::NC, 0, s>>>(
+        m, make_pcst<T>(pc), T(pc.inv_dt), Uo, Un, x, out, mm->d_flags);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    const int64_t nb = m.NB > 0 ? m.NB : 1;
+    if (MODE == MODE_RES)
+        bc_rows_kernel<D, T><<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(m, Un, Uo, out, pin);
+    else
+        bc_rows_kernel<D, T><<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(m, x, nullptr, out, pin);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_residual(const chns_mesh* m, const PhysConst& pc, const double* U_old, const double* U_new,
+                            double* R, int pin, cudaStream_t s) {
+    if (m->dm.dim == 2) return launch_rj<2, double, MODE_RES>(m, pc, U_old, U_new, nullptr, R, pin, s);
+    return launch_rj<3, double, MODE_RES>(m, pc, U_old, U_new, nullptr, R, pin, s);
+}
+
+cudaError_t launch_jvp64(const chns_mesh* m, const PhysConst& pc, const double* U_old, const double* U_lin,
+                         const double* x, double* y, int pin, cudaStream_t s) {
+    if (m->dm.dim == 2) return launch_rj<2, double, MODE_JVP>(m, pc, U_old, U_lin, x, y, pin, s);
+    return launch_rj<3, double, MODE_JVP>(m, pc, U_old, U_lin, x, y, pin, s);
+}
+
+cudaError_t launch_jvp32(const chns_mesh* m, const PhysConst& pc, const float* U_old, const float* U_lin,
+                         const float* x, float* y, int pin, cudaStream_t s) {
+    if (m->dm.dim == 2) return launch_rj<2, float, MODE_JVP>(m, pc, U_old, U_lin, x, y, pin, s);
+    return launch_rj<3, float, MODE_JVP>(m, pc, U_old, U_lin, x, y, pin, s);
+}
+
+cudaError_t launch_vjp(const chns_mesh* mm, const PhysConst& pc, const double* U_old, const double* U_lin,
+                       const double* w, double* gU_new, double* gU_old, double* gCn, int pin, cudaStream_t s) {
+    const DevMesh& m = mm->dm;
+    const int NF = m.nf;
+    cudaError_t err = cudaMemsetAsync(gU_new, 0, (size_t)m.N * NF * sizeof(double), s);
+    if (err == cudaSuccess && gU_old) err = cudaMemsetAsync(gU_old, 0, (size_t)m.N * NF * sizeof(double), s);
+    if (err == cudaSuccess && gCn) err = cudaMemsetAsync(gCn, 0, sizeof(double), s);
+    if (err != cudaSuccess) return err;
+    const int64_t nb = m.NB > 0 ? m.NB : 1;
+    if (m.dim == 2) {
+        const int EPB = 64 / 4;
+        elem_vjp_kernel<2><<<(unsigned)((m.E + EPB - 1) / EPB), 64, 0, s>>>(
+            m, make_pcst<double>(pc), pc.Cn, pc.inv_dt, U_old, U_lin, w, gU_new, gU_old, gCn, pin);
+        err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+        bc_vjp_kernel<2><<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(m, w, gU_new, gU_old, pin);
+    } else {
+        const int EPB = 64 / 8;
+        elem_vjp_kernel<3><<<(unsigned)((m.E + EPB - 1) / EPB), 64, 0, s>>>(
+            m, make_pcst<double>(pc), pc.Cn, pc.inv_dt, U_old, U_lin, w, gU_new, gU_old, gCn, pin);
+        err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+        bc_vjp_kernel<3><<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(m, w, gU_new, gU_old, pin);
+    }
+    return cudaGetLastError();
+}

@@ -1,0 +1,761 @@
+// Newton's method of Section 3.4, matrix-free: each Newton iteration solves
+// J dU = -R (Eq. newton_linear_system) with right-preconditioned restarted GMRES whose
+// operator is the J x element kernel (FP32 in mixed mode, FP64 otherwise) and whose
+// preconditioner is nodal block-Jacobi; orthogonalisation (classical Gram-Schmidt,
+// twice), dots, norms, the residual and the update stay FP64 on the device.  The
+// Hessenberg least-squares problem is solved on the host (one scalar read-back per
+// Krylov iteration).  Also: the consistent initial chemical potential by CG.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "chns_internal.h"
+#include "pointwise.cuh"
+#include "reduce.cuh"
+
+struct SolverWS {
+    int restart = 0;
+    int64_t n = 0, N = 0;
+    double* V = nullptr;     // (restart + 1) * n Arnoldi basis
+    double* w = nullptr;     // n
+    double* R = nullptr;     // n residual
+    double* dU = nullptr;    // n Newton update
+    double* z64 = nullptr;   // n
+    double* t64 = nullptr;   // n
+    float* Uo32 = nullptr;   // n
+    float* Us32 = nullptr;   // n
+    float* z32 = nullptr;    // n
+    float* y32 = nullptr;    // n
+    float* Pblk32 = nullptr; // N * nf * nf block diagonal (FP32 build)
+    double* Pblk64 = nullptr;
+    float* Pinv32 = nullptr; // inverted blocks
+    double* Pinv64 = nullptr;
+    double* sc = nullptr;    // device scalars
+    double* hsc = nullptr;   // pinned host scalars
+};
+
+void chns_solver_ws_free(SolverWS* ws) {
+    if (!ws) return;
+    cudaFree(ws->V);
+    cudaFree(ws->w);
+    cudaFree(ws->R);
+    cudaFree(ws->dU);
+    cudaFree(ws->z64);
+    cudaFree(ws->t64);
+    cudaFree(ws->Uo32);
+    cudaFree(ws->Us32);
+    cudaFree(ws->z32);
+    cudaFree(ws->y32);
+    cudaFree(ws->Pblk32);
+    cudaFree(ws->Pblk64);
+    cudaFree(ws->Pinv32);
+    cudaFree(ws->Pinv64);
+    cudaFree(ws->sc);
+    if (ws->hsc) cudaFreeHost(ws->hsc);
+    delete ws;
+}
+
+namespace {
+
+constexpr int MAXSC = 1024;
+
+chns_status ensure_ws(chns_mesh* m, int restart) {
+    SolverWS* ws = m->ws;
+    if (ws && ws->restart >= restart) return CHNS_OK;
+    if (ws) chns_solver_ws_free(ws);
+    m->ws = nullptr;
+    ws = new SolverWS();
+    ws->restart = restart;
+    ws->N = m->dm.N;
+    ws->n = m->dm.N * m->dm.nf;
+    const size_t n = (size_t)ws->n, nb = (size_t)m->dm.N * m->dm.nf * m->dm.nf;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](void** p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    };
+    A((void**)&ws->V, (size_t)(restart + 1) * n * sizeof(double));
+    A((void**)&ws->w, n * sizeof(double));
+    A((void**)&ws->R, n * sizeof(double));
+    A((void**)&ws->dU, n * sizeof(double));
+    A((void**)&ws->z64, n * sizeof(double));
+    A((void**)&ws->t64, n * sizeof(double));
+    A((void**)&ws->Uo32, n * sizeof(float));
+    A((void**)&ws->Us32, n * sizeof(float));
+    A((void**)&ws->z32, n * sizeof(float));
+    A((void**)&ws->y32, n * sizeof(float));
+    A((void**)&ws->Pblk32, nb * sizeof(float));
+    A((void**)&ws->Pblk64, nb * sizeof(double));
+    A((void**)&ws->Pinv32, nb * sizeof(float));
+    A((void**)&ws->Pinv64, nb * sizeof(double));
+    A((void**)&ws->sc, MAXSC * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&ws->hsc, MAXSC * sizeof(double));
+    if (e != cudaSuccess) {
+        chns_solver_ws_free(ws);
+        return chns_cuda_status(e, "cudaMalloc(solver workspace)");
+    }
+    m->ws = ws;
+    return CHNS_OK;
+}
+
+// ---------------- BLAS-1 ----------------
+__global__ void copy64_kernel(const double* __restrict__ a, double* __restrict__ b, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = a[i];
+}
+__global__ void to32_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+__global__ void to64_kernel(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (double)a[i];
+}
+// y = alpha * x (alpha read from device scalar sc[idx], optionally inverted)
+__global__ void scale_kernel(const double* __restrict__ x, double* __restrict__ y, int64_t n,
+                             const double* __restrict__ sc, int idx, double mult, int invert) {
+    const double s = invert ? mult / sc[idx] : mult * sc[idx];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = s * x[i];
+}
+// w -= sum_{j<k} h[j] V_j  (h in device memory)
+__global__ void gs_update_kernel(const double* __restrict__ V, int64_t ld, int k, const double* __restrict__ h,
+                                 double* __restrict__ w, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = w[i];
+        for (int j = 0; j < k; ++j) s -= h[j] * V[(size_t)j * ld + i];
+        w[i] = s;
+    }
+}
+// u = sum_{j<k} y[j] V_j (y host-provided via device scalars)
+__global__ void combine_kernel(const double* __restrict__ V, int64_t ld, int k, const double* __restrict__ y,
+                               double* __restrict__ u, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int j = 0; j < k; ++j) s += y[j] * V[(size_t)j * ld + i];
+        u[i] = s;
+    }
+}
+__global__ void axpy_kernel(double a, const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] += a * x[i];
+}
+// y = a*x + b*y
+__global__ void axpby_kernel(double a, const double* __restrict__ x, double b, double* __restrict__ y, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = a * x[i] + b * y[i];
+}
+
+int grid_for(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    const int64_t cap = 8 * (int64_t)chns_num_sms();
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+// ---------------- block-Jacobi preconditioner ----------------
+// Diagonal n_f x n_f block of every independent node, from the element-corner self
+// blocks d r_e[a] / d u_e[a] (forward mode with unit tangents).  Hanging corners are
+// skipped: the preconditioner is approximate there (it only affects convergence).
+template <int D, class T>
+__global__ void __launch_bounds__(128) pc_build_kernel(DevMesh m, PCst<T> c, T inv_dt, const T* __restrict__ Uo,
+                                                       const T* __restrict__ Un, T* __restrict__ blk);
+
+constexpr double GPc = 0.78867513459481288225, GMc = 0.21132486540518711775;
+
+template <int D, class T>
+struct PB {
+    T N, dN[D], d2N[D == 2 ? 1 : 3];
+};
+template <int D, class T>
+__device__ __forceinline__ PB<D, T> pbasis(int a, int q, T inv_h) {
+    T f[D], s[D];
+    for (int k = 0; k < D; ++k) {
+        f[k] = (((a >> k) & 1) == ((q >> k) & 1)) ? T(GPc) : T(GMc);
+        s[k] = ((a >> k) & 1) ? inv_h : -inv_h;
+    }
+    PB<D, T> b;
+    if constexpr (D == 2) {
+        b.N = f[0] * f[1];
+        b.dN[0] = s[0] * f[1];
+        b.dN[1] = f[0] * s[1];
+        b.d2N[0] = s[0] * s[1];
+    } else {
+        b.N = f[0] * f[1] * f[2];
+        b.dN[0] = s[0] * f[1] * f[2];
+        b.dN[1] = f[0] * s[1] * f[2];
+        b.dN[2] = f[0] * f[1] * s[2];
+        b.d2N[0] = s[0] * s[1] * f[2];
+        b.d2N[1] = s[0] * f[1] * s[2];
+        b.d2N[2] = f[0] * s[1] * s[2];
+    }
+    return b;
+}
+
+template <int D, class T>
+__global__ void __launch_bounds__(128) pc_build_kernel(DevMesh m, PCst<T> c, T inv_dt, const T* __restrict__ Uo,
+                                                       const T* __restrict__ Un, T* __restrict__ blk) {
+    constexpr int NC = 1 << D, NF = D + 3, NH = (D == 2) ? 1 : 3, EPB = 128 / NC;
+    __shared__ T s_ut[EPB][NC][NF], s_dd[EPB][NC][D + 1], s_ps[EPB][NC];
+    __shared__ int s_node[EPB][NC];
+    __shared__ unsigned char s_mask[EPB][NC];
+    const int le = threadIdx.x / NC, t = threadIdx.x % NC;
+    const int64_t e = (int64_t)blockIdx.x * EPB + le;
+    const bool valid = e < m.E;
+    T inv_h = T(1), detJ = T(0);
+    if (valid) {
+        const int ent = m.e2n[e * NC + t];
+        int p[4] = {0, 0, 0, 0}, np = 1;
+        if (ent >= 0) {
+            p[0] = ent;
+        } else {
+            const int4 hp = reinterpret_cast<const int4*>(m.hang)[-ent - 1];
+            p[0] = hp.x;
+            p[1] = hp.y;
+            p[2] = hp.z;
+            p[3] = hp.w;
+            np = hp.z < 0 ? 2 : 4;
+        }
+        const T wt = np == 1 ? T(1) : (np == 2 ? T(0.5) : T(0.25));
+        T so[NF], sn[NF], ps = T(0);
+        unsigned mask = 0;
+        for (int f = 0; f < NF; ++f) so[f] = sn[f] = T(0);
+        for (int j = 0; j < np; ++j) {
+            T o[NF], n[NF];
+            for (int f = 0; f < NF; ++f) {
+                o[f] = Uo[(size_t)p[j] * NF + f];
+                n[f] = Un[(size_t)p[j] * NF + f];
+                so[f] += wt * o[f];
+                sn[f] += wt * n[f];
+            }
+            const T avg = T(0.5) * (o[D + 1] + n[D + 1]);
+            if (avg <= T(1) && avg >= T(-1)) mask |= 1u << j;
+            ps += wt * (avg > T(1) ? T(1) : (avg < T(-1) ? T(-1) : avg));
+        }
+        for (int f = 0; f < NF; ++f) s_ut[le][t][f] = T(0.5) * (so[f] + sn[f]);
+        for (int i = 0; i < D; ++i) s_dd[le][t][i] = sn[i] - so[i];
+        s_dd[le][t][D] = sn[D + 1] - so[D + 1];
+        s_ps[le][t] = ps;
+        s_node[le][t] = ent;
+        s_mask[le][t] = (unsigned char)(mask & 1u);
+        const T h = T(ldexp(m.hi - m.lo, -(int)m.level[e]));
+        inv_h = T(1) / h;
+        detJ = (D == 2) ? T(0.25) * h * h : T(0.125) * h * h * h;
+    }
+    __syncwarp();
+    if (!valid) return;  // the remaining code uses only shuffles within the element's lanes
+    const int q = t;
+    const T g = T(4) * inv_h * inv_h;
+    // primal inputs at Gauss point q
+    QPIn<D, T> X;
+    {
+        X.p = X.phi = X.mu = X.phidt = X.divnew = X.ps = T(0);
+        for (int k = 0; k < D; ++k) {
+            X.v[k] = X.gp[k] = X.gphi[k] = X.gmu[k] = X.vdt[k] = X.gps[k] = T(0);
+            for (int j = 0; j < D; ++j) X.gv[k][j] = T(0);
+        }
+        for (int k = 0; k < NH; ++k) X.H[k] = T(0);
+        for (int a = 0; a < NC; ++a) {
+            const PB<D, T> b = pbasis<D, T>(a, q, inv_h);
+            const T* u = s_ut[le][a];
+            for (int i = 0; i < D; ++i) {
+                X.v[i] += b.N * u[i];
+                for (int k = 0; k < D; ++k) X.gv[i][k] += b.dN[k] * u[i];
+                X.vdt[i] += b.N * s_dd[le][a][i];
+                X.divnew += b.dN[i] * (u[i] + T(0.5) * s_dd[le][a][i]);
+            }
+            X.p += b.N * u[D];
+            X.phi += b.N * u[D + 1];
+            X.mu += b.N * u[D + 2];
+            for (int k = 0; k < D; ++k) {
+                X.gp[k] += b.dN[k] * u[D];
+                X.gphi[k] += b.dN[k] * u[D + 1];
+                X.gmu[k] += b.dN[k] * u[D + 2];
+                X.gps[k] += b.dN[k] * s_ps[le][a];
+            }
+            for (int k = 0; k < NH; ++k) X.H[k] += b.d2N[k] * u[D + 1];
+            X.phidt += b.N * s_dd[le][a][D];
+            X.ps += b.N * s_ps[le][a];
+        }
+        for (int i = 0; i < D; ++i) X.vdt[i] *= inv_dt;
+        X.phidt *= inv_dt;
+    }
+    const unsigned lanes = ((1u << NC) - 1u) << ((threadIdx.x & 31) & ~(NC - 1));
+    for (int a = 0; a < NC; ++a) {
+        const int node = s_node[le][a];
+        const PB<D, T> b = pbasis<D, T>(a, q, inv_h);
+        for (int gf = 0; gf < NF; ++gf) {
+            // unit tangent in field gf at corner a (averages move by 1/2, differences by 1)
+            QPIn<D, Dual<T>> XD;
+            const T hf = T(0.5);
+            for (int i = 0; i < D; ++i) {
+                XD.v[i] = Dual<T>(X.v[i], gf == i ? hf * b.N : T(0));
+                for (int k = 0; k < D; ++k) XD.gv[i][k] = Dual<T>(X.gv[i][k], gf == i ? hf * b.dN[k] : T(0));
+                XD.vdt[i] = Dual<T>(X.vdt[i], gf == i ? inv_dt * b.N : T(0));
+                XD.gp[i] = Dual<T>(X.gp[i], gf == D ? hf * b.dN[i] : T(0));
+                XD.gphi[i] = Dual<T>(X.gphi[i], gf == D + 1 ? hf * b.dN[i] : T(0));
+                XD.gmu[i] = Dual<T>(X.gmu[i], gf == D + 2 ? hf * b.dN[i] : T(0));
+                const T pst = (gf == D + 1 && s_mask[le][a]) ? hf * b.dN[i] : T(0);
+                XD.gps[i] = Dual<T>(X.gps[i], pst);
+            }
+            XD.p = Dual<T>(X.p, gf == D ? hf * b.N : T(0));
+            XD.phi = Dual<T>(X.phi, gf == D + 1 ? hf * b.N : T(0));
+            XD.mu = Dual<T>(X.mu, gf == D + 2 ? hf * b.N : T(0));
+            for (int k = 0; k < NH; ++k) XD.H[k] = Dual<T>(X.H[k], gf == D + 1 ? hf * b.d2N[k] : T(0));
+            XD.phidt = Dual<T>(X.phidt, gf == D + 1 ? inv_dt * b.N : T(0));
+            T dv = T(0);
+            if (gf < D) dv = b.dN[gf];
+            XD.divnew = Dual<T>(X.divnew, dv);
+            XD.ps = Dual<T>(X.ps, (gf == D + 1 && s_mask[le][a]) ? hf * b.N : T(0));
+            QPOut<D, Dual<T>> F;
+            pointwise<D, Dual<T>, T>(XD, c, g, F);
+            for (int f = 0; f < NF; ++f) {
+                T v = b.N * F.f0[f].d;
+                for (int k = 0; k < D; ++k) v += b.dN[k] * F.f1[f][k].d;
+                v *= detJ;
+                for (int off = NC / 2; off > 0; off >>= 1) v += __shfl_xor_sync(lanes, v, off);
+                if (q == 0 && node >= 0) atomicAdd(blk + ((size_t)node * NF + f) * NF + gf, v);
+            }
+        }
+    }
+}
+
+// Replace Dirichlet / pin rows by identity rows and invert every block (Gauss-Jordan
+// with partial pivoting in FP64).
+template <class TB, class TI>
+__global__ void pc_invert_kernel(DevMesh m, const TB* __restrict__ blk, TI* __restrict__ inv, int pin) {
+    const int NF = m.nf, D = m.dim;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= m.N) return;
+    double A[6][12];
+    for (int i = 0; i < NF; ++i)
+        for (int j = 0; j < NF; ++j) {
+            A[i][j] = (double)blk[((size_t)n * NF + i) * NF + j];
+            A[i][NF + j] = (i == j) ? 1.0 : 0.0;
+        }
+    const bool bnd = m.nflag[n] & 1;
+    for (int i = 0; i < NF; ++i) {
+        const bool idrow = (i < D && bnd) || (i == D && pin && n == 0);
+        if (idrow)
+            for (int j = 0; j < NF; ++j) A[i][j] = (i == j) ? 1.0 : 0.0;
+    }
+    for (int col = 0; col < NF; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < NF; ++r)
+            if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+        if (piv != col)
+            for (int j = 0; j < 2 * NF; ++j) {
+                const double tmp = A[col][j];
+                A[col][j] = A[piv][j];
+                A[piv][j] = tmp;
+            }
+        double d = A[col][col];
+        if (d == 0.0) d = 1e-300;
+        const double inv_d = 1.0 / d;
+        for (int j = 0; j < 2 * NF; ++j) A[col][j] *= inv_d;
+        for (int r = 0; r < NF; ++r) {
+            if (r == col) continue;
+            const double f = A[r][col];
+            if (f != 0.0)
+                for (int j = 0; j < 2 * NF; ++j) A[r][j] -= f * A[col][j];
+        }
+    }
+    for (int i = 0; i < NF; ++i)
+        for (int j = 0; j < NF; ++j) inv[((size_t)n * NF + i) * NF + j] = (TI)A[i][NF + j];
+}
+
+// z = P^{-1} v per node (FP64 input; output type TO, arithmetic in the storage type's
+// precision promoted to FP64 for the final update)
+template <class TI, class TO>
+__global__ void pc_apply_kernel(int64_t N, int NF, const TI* __restrict__ inv, const double* __restrict__ v,
+                                TO* __restrict__ z) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    double x[6];
+    for (int j = 0; j < NF; ++j) x[j] = v[(size_t)n * NF + j];
+    for (int i = 0; i < NF; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < NF; ++j) s += (double)inv[((size_t)n * NF + i) * NF + j] * x[j];
+        z[(size_t)n * NF + i] = (TO)s;
+    }
+}
+
+// ---------------- initial chemical potential (mass-matrix CG) ----------------
+// b_a = sum_q |J| (N_a psi'(phi_q) + Cn^2 grad N_a . grad phi_q)  and  y = M x, with the
+// consistent Q1 mass matrix; hanging corners via their parents.
+template <int D, int MODE>
+__global__ void mu_kernel(DevMesh m, double Cn2, const double* __restrict__ U, const double* __restrict__ x,
+                          double* __restrict__ y) {
+    constexpr int NC = 1 << D, NF = D + 3;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m.E) return;
+    const double h = ldexp(m.hi - m.lo, -(int)m.level[e]);
+    const double inv_h = 1.0 / h, detJ = (D == 2) ? 0.25 * h * h : 0.125 * h * h * h;
+    int par[NC][4], np[NC];
+    double u[NC];
+    for (int a = 0; a < NC; ++a) {
+        const int ent = m.e2n[e * NC + a];
+        if (ent >= 0) {
+            np[a] = 1;
+            par[a][0] = ent;
+        } else {
+            const int4 hp = reinterpret_cast<const int4*>(m.hang)[-ent - 1];
+            par[a][0] = hp.x;
+            par[a][1] = hp.y;
+            par[a][2] = hp.z;
+            par[a][3] = hp.w;
+            np[a] = hp.z < 0 ? 2 : 4;
+        }
+        const double w = np[a] == 1 ? 1.0 : (np[a] == 2 ? 0.5 : 0.25);
+        double s = 0.0;
+        for (int j = 0; j < np[a]; ++j)
+            s += w * (MODE == 0 ? U[(size_t)par[a][j] * NF + D + 1] : x[par[a][j]]);
+        u[a] = s;
+    }
+    double r[NC];
+    for (int a = 0; a < NC; ++a) r[a] = 0.0;
+    for (int q = 0; q < NC; ++q) {
+        double val = 0.0, grad[D];
+        for (int k = 0; k < D; ++k) grad[k] = 0.0;
+        PB<D, double> B[NC];
+        for (int a = 0; a < NC; ++a) {
+            B[a] = pbasis<D, double>(a, q, inv_h);
+            val += B[a].N * u[a];
+            for (int k = 0; k < D; ++k) grad[k] += B[a].dN[k] * u[a];
+        }
+        for (int a = 0; a < NC; ++a) {
+            double t;
+            if (MODE == 0) {
+                t = B[a].N * (val * val * val - val);
+                for (int k = 0; k < D; ++k) t += Cn2 * B[a].dN[k] * grad[k];
+            } else {
+                t = B[a].N * val;
+            }
+            r[a] += detJ * t;
+        }
+    }
+    for (int a = 0; a < NC; ++a) {
+        const double w = np[a] == 1 ? 1.0 : (np[a] == 2 ? 0.5 : 0.25);
+        for (int j = 0; j < np[a]; ++j) atomicAdd(y + par[a][j], w * r[a]);
+    }
+}
+
+__global__ void extract_mu_kernel(const double* __restrict__ U, int NF, int f, int64_t N, double* __restrict__ out) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n < N) out[n] = U[(size_t)n * NF + f];
+}
+__global__ void insert_mu_kernel(const double* __restrict__ in, int NF, int f, int64_t N, double* __restrict__ U) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n < N) U[(size_t)n * NF + f] = in[n];
+}
+__global__ void fill_kernel(double* __restrict__ x, double v, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = v;
+}
+__global__ void jacobi_kernel(const double* __restrict__ d, const double* __restrict__ r, double* __restrict__ z,
+                              int64_t N) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n < N) z[n] = r[n] / d[n];
+}
+
+template <class R>
+PCst<R> pcst_from(const PhysConst& pc) {
+    PCst<R> c;
+    c.alpha = R(pc.alpha);
+    c.beta = R(pc.beta);
+    c.gamma = R(pc.gamma);
+    c.xi = R(pc.xi);
+    c.Jc = R((pc.rho_minus - pc.rho_plus) / (2.0 * pc.rho_plus * pc.Cn));
+    c.inv_Pe = R(pc.inv_Pe);
+    c.inv_We = R(pc.inv_We);
+    c.inv_Re = R(pc.inv_Re);
+    c.inv_Fr = R(pc.inv_Fr);
+    c.Cn_We = R(pc.Cn * pc.inv_We);
+    c.inv_PeCn = R(1.0 / (pc.Pe * pc.Cn));
+    c.Cn2 = R(pc.Cn * pc.Cn);
+    c.Pe = R(pc.Pe);
+    c.Re = R(pc.Re);
+    c.four_over_dt2 = R(pc.four_over_dt2);
+    c.C_I = R(pc.C_I);
+    c.C_phi = R(pc.C_phi);
+    return c;
+}
+
+struct Ctx {
+    chns_mesh* m;
+    SolverWS* ws;
+    cudaStream_t s;
+    int64_t n;
+    int g;
+};
+
+// host read of k device scalars (synchronises)
+chns_status read_sc(Ctx& c, const double* dev, int k, double* host) {
+    CHNS_CUDA(cudaMemcpyAsync(c.ws->hsc, dev, k * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+    CHNS_CUDA(cudaStreamSynchronize(c.s));
+    std::memcpy(host, c.ws->hsc, k * sizeof(double));
+    return CHNS_OK;
+}
+
+chns_status dot_host(Ctx& c, const double* a, const double* b, double* out) {
+    CHNS_CUDA(launch_dot(c.m, a, b, c.n, c.ws->sc, c.s));
+    return read_sc(c, c.ws->sc, 1, out);
+}
+
+template <int D, class T>
+cudaError_t pc_build_launch(const chns_mesh* m, const PhysConst& pc, const T* Uo, const T* Un, T* blk,
+                            cudaStream_t s) {
+    constexpr int NC = 1 << D, EPB = 128 / NC;
+    cudaError_t e = cudaMemsetAsync(blk, 0, (size_t)m->dm.N * m->dm.nf * m->dm.nf * sizeof(T), s);
+    if (e != cudaSuccess) return e;
+    pc_build_kernel<D, T><<<(unsigned)((m->dm.E + EPB - 1) / EPB), 128, 0, s>>>(m->dm, pcst_from<T>(pc),
+                                                                               T(pc.inv_dt), Uo, Un, blk);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* p, const chns_solver_opts* o,
+                                        const double* U_old, double* U, chns_stats* stats, void* stream) {
+    chns_mesh* m = const_cast<chns_mesh*>(mc);
+    PhysConst pc;
+    chns_status st = chns_check_params(mc, p, &pc);
+    if (st != CHNS_OK) return st;
+    if (!o || !U_old || !U) { chns_set_error("null argument"); return CHNS_EINVAL; }
+    if (o->restart < 1 || o->restart > MAXSC / 4 || o->max_krylov < 1 || o->max_newton < 0 ||
+        (o->precision != 0 && o->precision != 1)) {
+        chns_set_error("bad solver options (restart in [1, 256], max_krylov >= 1, precision 0/1)");
+        return CHNS_EINVAL;
+    }
+    if ((st = ensure_ws(m, o->restart)) != CHNS_OK) return st;
+    SolverWS* ws = m->ws;
+    Ctx c{m, ws, (cudaStream_t)stream, ws->n, 0};
+    c.g = grid_for(c.n);
+    const int D = m->dm.dim, NF = m->dm.nf, mres = o->restart;
+    const bool mixed = o->precision == 1;
+    const int pin = p->pin_pressure;
+    const int gN = (int)((m->dm.N + 127) / 128);
+    chns_stats S;
+    std::memset(&S, 0, sizeof(S));
+    S.reason = CHNS_OK;
+
+    CHNS_CUDA(cudaMemsetAsync(m->d_flags, 0, sizeof(unsigned int), c.s));
+    copy64_kernel<<<c.g, 256, 0, c.s>>>(U_old, U, c.n);
+    if (mixed) to32_kernel<<<c.g, 256, 0, c.s>>>(U_old, ws->Uo32, c.n);
+    CHNS_CUDA(cudaGetLastError());
+
+    std::vector<double> H((size_t)(mres + 1) * mres), cs(mres), sn(mres), gv(mres + 1), y(mres);
+    double r0 = 0.0, rn = 0.0;
+    chns_status result = CHNS_OK;
+    for (int it = 0;; ++it) {
+        CHNS_CUDA(launch_residual(m, pc, U_old, U, ws->R, pin, c.s));
+        if ((st = dot_host(c, ws->R, ws->R, &rn)) != CHNS_OK) return st;
+        unsigned int flag = 0;
+        CHNS_CUDA(cudaMemcpy(&flag, m->d_flags, sizeof(unsigned int), cudaMemcpyDeviceToHost));
+        rn = std::sqrt(rn);
+        if (it == 0) r0 = rn;
+        S.newton_its = it;
+        S.res0 = r0;
+        S.res_final = rn;
+        if (flag & 1u) { chns_set_error("a tau_m radicand was not positive"); result = CHNS_ETAU; break; }
+        if (!std::isfinite(rn)) { chns_set_error("non-finite residual norm"); result = CHNS_ENAN; break; }
+        if (rn <= o->atol || rn <= o->rtol * r0) break;
+        if (it >= o->max_newton) { chns_set_error("Newton did not converge"); result = CHNS_ENOCONV; break; }
+
+        // linearisation state and preconditioner
+        if (mixed) {
+            to32_kernel<<<c.g, 256, 0, c.s>>>(U, ws->Us32, c.n);
+            cudaError_t e = (D == 2) ? pc_build_launch<2, float>(m, pc, ws->Uo32, ws->Us32, ws->Pblk32, c.s)
+                                     : pc_build_launch<3, float>(m, pc, ws->Uo32, ws->Us32, ws->Pblk32, c.s);
+            CHNS_CUDA(e);
+            pc_invert_kernel<float, float><<<gN, 128, 0, c.s>>>(m->dm, ws->Pblk32, ws->Pinv32, pin);
+        } else {
+            cudaError_t e = (D == 2) ? pc_build_launch<2, double>(m, pc, U_old, U, ws->Pblk64, c.s)
+                                     : pc_build_launch<3, double>(m, pc, U_old, U, ws->Pblk64, c.s);
+            CHNS_CUDA(e);
+            pc_invert_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm, ws->Pblk64, ws->Pinv64, pin);
+        }
+        CHNS_CUDA(cudaGetLastError());
+
+        // GMRES(mres) on J dU = -R, right preconditioned, from dU = 0
+        CHNS_CUDA(cudaMemsetAsync(ws->dU, 0, c.n * sizeof(double), c.s));
+        const double bnorm = rn;
+        double rnorm = bnorm;
+        int kry = 0;
+        // r = -R
+        axpby_kernel<<<c.g, 256, 0, c.s>>>(-1.0, ws->R, 0.0, ws->w, c.n);
+        while (true) {
+            // V0 = r / ||r||
+            double beta = rnorm;
+            axpby_kernel<<<c.g, 256, 0, c.s>>>(1.0 / beta, ws->w, 0.0, ws->V, c.n);
+            std::fill(gv.begin(), gv.end(), 0.0);
+            gv[0] = beta;
+            int j = 0;
+            bool done = false;
+            for (; j < mres && kry < o->max_krylov; ++j, ++kry) {
+                double* Vj = ws->V + (size_t)j * c.n;
+                // w = J M^{-1} V_j
+                if (mixed) {
+                    pc_apply_kernel<float, float><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv32, Vj, ws->z32);
+                    CHNS_CUDA(launch_jvp32(m, pc, ws->Uo32, ws->Us32, ws->z32, ws->y32, pin, c.s));
+                    to64_kernel<<<c.g, 256, 0, c.s>>>(ws->y32, ws->w, c.n);
+                } else {
+                    pc_apply_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv64, Vj, ws->z64);
+                    CHNS_CUDA(launch_jvp64(m, pc, U_old, U, ws->z64, ws->w, pin, c.s));
+                }
+                S.jvp_calls++;
+                // classical Gram-Schmidt, twice
+                CHNS_CUDA(launch_multidot(m, ws->V, c.n, j + 1, ws->w, c.n, ws->sc, c.s));
+                gs_update_kernel<<<c.g, 256, 0, c.s>>>(ws->V, c.n, j + 1, ws->sc, ws->w, c.n);
+                CHNS_CUDA(launch_multidot(m, ws->V, c.n, j + 1, ws->w, c.n, ws->sc + 256, c.s));
+                gs_update_kernel<<<c.g, 256, 0, c.s>>>(ws->V, c.n, j + 1, ws->sc + 256, ws->w, c.n);
+                CHNS_CUDA(launch_dot(m, ws->w, ws->w, c.n, ws->sc + 512, c.s));
+                double hs[2 * 256 + 1];
+                CHNS_CUDA(cudaMemcpyAsync(ws->hsc, ws->sc, 513 * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+                CHNS_CUDA(cudaStreamSynchronize(c.s));
+                std::memcpy(hs, ws->hsc, 513 * sizeof(double));
+                const double hn = std::sqrt(hs[512]);
+                for (int i = 0; i <= j; ++i) H[(size_t)i * mres + j] = hs[i] + hs[256 + i];
+                H[(size_t)(j + 1) * mres + j] = hn;
+                if (!std::isfinite(hn)) { chns_set_error("non-finite Arnoldi vector"); S.reason = CHNS_EBREAKDOWN; result = CHNS_EBREAKDOWN; break; }
+                // Givens rotations
+                for (int i = 0; i < j; ++i) {
+                    const double a = H[(size_t)i * mres + j], b = H[(size_t)(i + 1) * mres + j];
+                    H[(size_t)i * mres + j] = cs[i] * a + sn[i] * b;
+                    H[(size_t)(i + 1) * mres + j] = -sn[i] * a + cs[i] * b;
+                }
+                const double a = H[(size_t)j * mres + j], b = H[(size_t)(j + 1) * mres + j];
+                const double r = std::hypot(a, b);
+                cs[j] = r > 0 ? a / r : 1.0;
+                sn[j] = r > 0 ? b / r : 0.0;
+                H[(size_t)j * mres + j] = r;
+                H[(size_t)(j + 1) * mres + j] = 0.0;
+                gv[j + 1] = -sn[j] * gv[j];
+                gv[j] = cs[j] * gv[j];
+                rnorm = std::fabs(gv[j + 1]);
+                if (hn > 0.0)
+                    axpby_kernel<<<c.g, 256, 0, c.s>>>(1.0 / hn, ws->w, 0.0, ws->V + (size_t)(j + 1) * c.n, c.n);
+                if (rnorm <= o->krylov_rtol * bnorm || hn == 0.0) {
+                    ++j;
+                    ++kry;
+                    done = true;
+                    break;
+                }
+            }
+            if (result != CHNS_OK) break;
+            // y = H^{-1} g, dU += M^{-1} V y
+            const int k = j;
+            for (int i = k - 1; i >= 0; --i) {
+                double s = gv[i];
+                for (int l = i + 1; l < k; ++l) s -= H[(size_t)i * mres + l] * y[l];
+                y[i] = s / H[(size_t)i * mres + i];
+            }
+            std::memcpy(ws->hsc, y.data(), k * sizeof(double));
+            CHNS_CUDA(cudaMemcpyAsync(ws->sc, ws->hsc, k * sizeof(double), cudaMemcpyHostToDevice, c.s));
+            combine_kernel<<<c.g, 256, 0, c.s>>>(ws->V, c.n, k, ws->sc, ws->t64, c.n);
+            if (mixed)
+                pc_apply_kernel<float, double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv32, ws->t64, ws->z64);
+            else
+                pc_apply_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv64, ws->t64, ws->z64);
+            axpy_kernel<<<c.g, 256, 0, c.s>>>(1.0, ws->z64, ws->dU, c.n);
+            CHNS_CUDA(cudaGetLastError());
+            if (done || kry >= o->max_krylov) break;
+            // restart: r = -R - J dU (same operator as the Arnoldi process)
+            if (mixed) {
+                to32_kernel<<<c.g, 256, 0, c.s>>>(ws->dU, ws->z32, c.n);
+                CHNS_CUDA(launch_jvp32(m, pc, ws->Uo32, ws->Us32, ws->z32, ws->y32, pin, c.s));
+                to64_kernel<<<c.g, 256, 0, c.s>>>(ws->y32, ws->w, c.n);
+            } else {
+                CHNS_CUDA(launch_jvp64(m, pc, U_old, U, ws->dU, ws->w, pin, c.s));
+            }
+            S.jvp_calls++;
+            axpby_kernel<<<c.g, 256, 0, c.s>>>(-1.0, ws->R, -1.0, ws->w, c.n);
+            double rr;
+            if ((st = dot_host(c, ws->w, ws->w, &rr)) != CHNS_OK) return st;
+            rnorm = std::sqrt(rr);
+            if (rnorm <= o->krylov_rtol * bnorm) break;
+        }
+        S.krylov_its += kry;
+        if (result != CHNS_OK) break;
+        axpy_kernel<<<c.g, 256, 0, c.s>>>(1.0, ws->dU, U, c.n);
+        double du;
+        if ((st = dot_host(c, ws->dU, ws->dU, &du)) != CHNS_OK) return st;
+        S.du_norm = std::sqrt(du);
+    }
+    S.reason = result;
+    if (stats) *stats = S;
+    return result;
+}
+
+extern "C" chns_status chns_initial_mu(const chns_mesh* mc, const chns_params* p, double* U, void* stream) {
+    chns_mesh* m = const_cast<chns_mesh*>(mc);
+    PhysConst pc;
+    chns_status st = chns_check_params(mc, p, &pc);
+    if (st != CHNS_OK) return st;
+    if (!U) { chns_set_error("null argument"); return CHNS_EINVAL; }
+    if ((st = ensure_ws(m, m->ws ? m->ws->restart : 1)) != CHNS_OK) return st;
+    SolverWS* ws = m->ws;
+    const int64_t N = m->dm.N;
+    Ctx c{m, ws, (cudaStream_t)stream, N, grid_for(N)};
+    const int D = m->dm.dim, NF = m->dm.nf;
+    const int gE = (int)((m->dm.E + 127) / 128), gN = (int)((N + 255) / 256);
+    // work vectors (each N doubles) carved from the Krylov workspace
+    double* b = ws->w;
+    double* x = ws->R;
+    double* r = ws->dU;
+    double* z = ws->z64;
+    double* q = ws->t64;
+    double* dg = ws->V;
+    double* pvec = ws->V + N;
+    const double Cn2 = p->Cn * p->Cn;
+    cudaError_t e = cudaMemsetAsync(b, 0, N * sizeof(double), c.s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dg, 0, N * sizeof(double), c.s);
+    if (e != cudaSuccess) return chns_cuda_status(e, "cudaMemsetAsync");
+    if (D == 2) {
+        mu_kernel<2, 0><<<gE, 128, 0, c.s>>>(m->dm, Cn2, U, nullptr, b);
+    } else {
+        mu_kernel<3, 0><<<gE, 128, 0, c.s>>>(m->dm, Cn2, U, nullptr, b);
+    }
+    // Jacobi scaling by the row sums of M (the integral of each basis function, > 0)
+    fill_kernel<<<c.g, 256, 0, c.s>>>(q, 1.0, N);
+    if (D == 2)
+        mu_kernel<2, 1><<<gE, 128, 0, c.s>>>(m->dm, Cn2, U, q, dg);
+    else
+        mu_kernel<3, 1><<<gE, 128, 0, c.s>>>(m->dm, Cn2, U, q, dg);
+    CHNS_CUDA(cudaGetLastError());
+    // CG from x = 0
+    CHNS_CUDA(cudaMemsetAsync(x, 0, N * sizeof(double), c.s));
+    copy64_kernel<<<c.g, 256, 0, c.s>>>(b, r, N);
+    jacobi_kernel<<<gN, 256, 0, c.s>>>(dg, r, z, N);
+    copy64_kernel<<<c.g, 256, 0, c.s>>>(z, pvec, N);
+    double rz, bb;
+    if ((st = dot_host(c, r, z, &rz)) != CHNS_OK) return st;
+    if ((st = dot_host(c, b, b, &bb)) != CHNS_OK) return st;
+    const double tol = 1e-14 * std::sqrt(bb);
+    int it = 0;
+    for (; it < 1000 && bb > 0.0; ++it) {
+        CHNS_CUDA(cudaMemsetAsync(q, 0, N * sizeof(double), c.s));
+        if (D == 2)
+            mu_kernel<2, 1><<<gE, 128, 0, c.s>>>(m->dm, Cn2, U, pvec, q);
+        else
+            mu_kernel<3, 1><<<gE, 128, 0, c.s>>>(m->dm, Cn2, U, pvec, q);
+        double pq, rr;
+        if ((st = dot_host(c, pvec, q, &pq)) != CHNS_OK) return st;
+        const double alpha = rz / pq;
+        axpy_kernel<<<c.g, 256, 0, c.s>>>(alpha, pvec, x, N);
+        axpy_kernel<<<c.g, 256, 0, c.s>>>(-alpha, q, r, N);
+        if ((st = dot_host(c, r, r, &rr)) != CHNS_OK) return st;
+        if (!std::isfinite(rr)) { chns_set_error("non-finite CG residual"); return CHNS_ENAN; }
+        if (std::sqrt(rr) <= tol) break;
+        jacobi_kernel<<<gN, 256, 0, c.s>>>(dg, r, z, N);
+        double rz2;
+        if ((st = dot_host(c, r, z, &rz2)) != CHNS_OK) return st;
+        axpby_kernel<<<c.g, 256, 0, c.s>>>(1.0, z, rz2 / rz, pvec, N);
+        rz = rz2;
+    }
+    insert_mu_kernel<<<gN, 256, 0, c.s>>>(x, NF, D + 2, N, U);
+    CHNS_CUDA(cudaGetLastError());
+    CHNS_CUDA(cudaStreamSynchronize(c.s));
+    if (it >= 1000) { chns_set_error("mass-matrix CG did not converge"); return CHNS_ENOCONV; }
+    return CHNS_OK;
+}

@@ -1,0 +1,80 @@
+"""The C-ABI library loads, exports every function declared in include/chns.h, and
+rejects invalid leaf lists on the host before touching the GPU."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "chns.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(chns_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def chns():
+    import paper_2009_06628_gb300 as chns
+    if not os.path.exists(chns.LIB_PATH):
+        from paper_2009_06628_gb300 import build
+        build.build()
+    chns.load()
+    return chns
+
+
+def test_every_declared_symbol_is_exported(chns):
+    names = _declared_functions()
+    assert len(names) >= 14
+    lib = chns.load()
+    for n in names:
+        assert hasattr(lib, n), n
+    bound = {s[0] for s in chns.SIGNATURES}
+    assert set(names) <= bound, set(names) - bound
+
+
+def test_rejects_unsorted_leaves(chns):
+    leaves = synth.uniform_leaves(2, 3)[::-1].copy()
+    with pytest.raises(chns.ChnsError) as e:
+        chns.Mesh(2, 3, leaves)
+    assert e.value.name == "CHNS_ENOTSORTED"
+
+
+@pytest.mark.parametrize("cut", ["gap", "overlap", "misaligned"])
+def test_rejects_incomplete_leaves(chns, cut):
+    leaves = synth.uniform_leaves(3, 2)
+    if cut == "gap":
+        leaves = leaves[np.arange(leaves.shape[0]) != 5].copy()
+    elif cut == "overlap":
+        extra = leaves.copy()
+        extra[:, 3] = 1
+        leaves = np.concatenate([leaves[:1], np.array([[0, 0, 0, 1]], dtype=np.int32), leaves[1:]])
+    else:
+        leaves = leaves.copy()
+        leaves[3, 0] += 1
+    with pytest.raises(chns.ChnsError) as e:
+        chns.Mesh(3, 2, leaves)
+    assert e.value.name in ("CHNS_ENOTCOMPLETE", "CHNS_ENOTSORTED")
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_rejects_unbalanced_octree(chns, dim):
+    # one quadrant refined two levels beyond its neighbours, no balancing
+    leaves = synth.refine_leaves(dim, 1, 3, lambda lo, hi, lev: np.all(hi <= 0.5 + 1e-12, axis=1))
+    with pytest.raises(chns.ChnsError) as e:
+        chns.Mesh(dim, 3, leaves)
+    assert e.value.name == "CHNS_ENOTBALANCED"
+
+
+def test_rejects_bad_arguments(chns):
+    leaves = synth.uniform_leaves(2, 2)
+    with pytest.raises(chns.ChnsError) as e:
+        chns.Mesh(4, 2, leaves)
+    assert e.value.name == "CHNS_EINVAL"
+    with pytest.raises(chns.ChnsError) as e:
+        chns.Mesh(2, 2, leaves, lo=1.0, hi=0.0)
+    assert e.value.name == "CHNS_EINVAL"
