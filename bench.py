@@ -1,0 +1,326 @@
+"""Benchmark of the matrix-free CHNS hot path on one GB300 (replicas on N GPUs).
+
+Workload: the 3D drop on a uniform level-6 octree (64^3 trilinear hexes, 274,625
+nodes x 6 DOF = 1,647,750 DOF), density and viscosity ratios 10, Re=100, We=10, Pe=100,
+Fr=1 (gravity along -z), Cn=0.02, dt=5e-4; phi0 a tanh drop of radius 0.2, v0 a
+seeded divergence-free sum of 8 Fourier modes with max |v| = 0.1, mu0 from the
+discrete potential equation.
+
+One step = one mixed-precision Newton step (FP64 residual, FP32 block-Jacobi build,
+GMRES with the FP32 J x kernel, FP64 classical Gram-Schmidt, FP64 update) from the
+same U^k, to a relative residual of 1e-9.  value = DOF x (J x applications) / step
+time, i.e. the J x throughput sustained by the whole Newton step.  The dominant
+kernel's roofline uses the CUDA-event time of the J x launches taken inside the step.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+LEVEL = 6
+DIM = 3
+WORKLOAD = ("3D CHNS drop, uniform octree level 6 (64^3 Q1 hexes, 274,625 nodes x 6 DOF), "
+            "rho/eta ratios 10, Re=100 We=10 Pe=100 Fr=1 Cn=0.02 dt=5e-4; one mixed-precision "
+            "Newton step to rel. residual 1e-9 per step")
+METRIC = "CHNS J·x GDOF/s & % HBM roofline; mixed vs FP64 Newton step time at ≤1e-9 rel"
+# Executed FP32 floating-point operations of one J x element (ncu: 2 x FFMA + FADD + FMUL
+# thread instructions of the FP32 J x kernel divided by the element count).
+FLOPS_PER_ELEMENT_JVP32 = None
+# Derived FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
+
+
+def workload_state(x):
+    U = np.zeros((x.shape[0], DIM + 3))
+    cfg = synth.config_params("drop3d")
+    U[:, DIM + 1] = synth.drop_phi(x, [[0.5, 0.5, 0.5]], [0.2], cfg["Cn"])
+    U[:, :DIM] = synth.fourier_velocity(x, 8, 2, 0.1)
+    bnd = np.any((x <= 0.0) | (x >= 1.0), axis=1)
+    U[bnd, :DIM] = 0.0
+    return cfg, U
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, gpu):
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline_oracle(seconds_hint=True):
+    """The oracle's J x (torch forward mode, FP64, host cores) on a bounded sample of the
+    same workload: the level-5 uniform mesh (32^3 hexes, 35,937 nodes x 6 DOF)."""
+    from oracle import Mesh as OMesh, Oracle, Params as OParams
+    level = 5
+    om = OMesh(DIM, level, synth.uniform_leaves(DIM, level))
+    o = Oracle(om)
+    cfg, U = workload_state(om.x)
+    prm = OParams(**cfg)
+    Ut = torch.tensor(U)
+    Un = Ut + 1e-4 * torch.tensor(synth.random_vectors(U.size, 1, 7)[0]).reshape(U.shape)
+    Un[torch.tensor(om.boundary), :DIM] = 0.0
+    x = torch.tensor(synth.random_vectors(U.size, 1, 8)[0]).reshape(U.shape)
+    o.jvp(prm, Ut, Un, x)  # warm-up
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        o.jvp(prm, Ut, Un, x)
+        reps += 1
+        if time.perf_counter() - t0 > 10.0 or reps >= 5:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    dof = U.size
+    return {"value": dof / dt / 1e9, "unit": "GDOF/s", "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"oracle J x (FP64 torch forward mode) on the level-5 uniform mesh, {dof} DOF, "
+                      f"{reps} applications, {dt:.2f} s each"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from oracle import Mesh as OMesh, Oracle, Params as OParams
+    level = 5
+    om = OMesh(DIM, level, synth.uniform_leaves(DIM, level))
+    o = Oracle(om)
+    cfg, U = workload_state(om.x)
+    prm = OParams(**cfg)
+    Ut = torch.tensor(U)
+    Un = Ut.clone()
+    x = torch.tensor(synth.random_vectors(U.size, 1, 8)[0]).reshape(U.shape)
+    for _ in range(args.warmup):
+        o.jvp(prm, Ut, Un, x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.jvp(prm, Ut, Un, x)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = U.size / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GDOF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "level-5 uniform mesh (32^3 hexes), one oracle J x per step"},
+            "cpu_baseline": {"value": v, "unit": "GDOF/s", "cores": torch.get_num_threads(), "kind": "oracle",
+                             "sample": "oracle J x on the level-5 uniform mesh (35,937 nodes x 6 DOF) per step"},
+            "e2e": {"value": v, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_profile(args):
+    """One kernel of the hot path, --reps launches, on the uniform mesh of --level."""
+    import paper_2009_06628_gb300 as chns
+    leaves = synth.uniform_leaves(DIM, args.level)
+    gm = chns.Mesh(DIM, args.level, leaves)
+    cfg, U = workload_state(gm.node_x())
+    prm = chns.Params.make(**cfg)
+    U0 = torch.tensor(U, device="cuda")
+    Un = U0 + 1e-4 * torch.randn(U0.shape, device="cuda", dtype=torch.float64,
+                                 generator=torch.Generator(device="cuda").manual_seed(7))
+    x = torch.randn(U0.shape, device="cuda", dtype=torch.float64, generator=torch.Generator(device="cuda").manual_seed(8))
+    for _ in range(args.reps):
+        if args.profile == "jvp32":
+            chns.jvp(gm, prm, U0.float(), Un.float(), x.float())
+        elif args.profile == "jvp64":
+            chns.jvp(gm, prm, U0, Un, x)
+        elif args.profile == "residual":
+            chns.residual(gm, prm, U0, Un)
+        else:
+            chns.vjp(gm, prm, U0, Un, x)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile, "level": args.level, "elements": gm.E, "nodes": gm.N}))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--profile", choices=["jvp32", "jvp64", "residual", "vjp"],
+                    help="run only this kernel --reps times on a uniform mesh of --level (for ncu)")
+    ap.add_argument("--level", type=int, default=LEVEL)
+    ap.add_argument("--reps", type=int, default=3)
+    args = ap.parse_args()
+    if args.profile:
+        return run_profile(args)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    import paper_2009_06628_gb300 as chns
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    leaves = synth.uniform_leaves(DIM, LEVEL)
+    gm = chns.Mesh(DIM, LEVEL, leaves)
+    cfg, U = workload_state(gm.node_x())
+    prm = chns.Params.make(**cfg)
+    U0 = torch.tensor(U, device=dev)
+    chns.initial_mu(gm, prm, U0)
+    dof = U0.numel()
+    opts = chns.SolverOpts.make(rtol=1e-9, atol=1e-14, krylov_rtol=1e-3, precision=1, restart=60, max_krylov=3000)
+    U1 = torch.empty_like(U0)
+    for _ in range(args.warmup):
+        chns.newton_step(gm, prm, opts, U0, U1)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K mixed Newton steps from the same U^k ----
+    clocks = ClockSampler(local)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = chns.kernel_launches()
+    ev0.record(stream)
+    jvp_calls, jvp_ms, stats = 0, 0.0, []
+    for _ in range(args.steps):
+        _, st = chns.newton_step(gm, prm, opts, U0, U1)
+        jvp_calls += st.jvp_calls
+        jvp_ms += st.jvp_ms
+        stats.append(st.as_dict())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = chns.kernel_launches() - launches0
+    clk = clocks.stop()
+    t_ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t)
+        cnt = torch.tensor([float(jvp_calls)], device=dev)
+        dist.all_reduce(cnt)
+        total_jvp = float(cnt)
+    else:
+        total_jvp = float(jvp_calls)
+    value = dof * total_jvp / (t_ms * 1e-3) / 1e9
+
+    # ---- end to end through the public API with host buffers ----
+    host_in = torch.tensor(U0.cpu().numpy()).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    Ud = torch.empty_like(U0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    e2e_jvp = 0
+    for _ in range(args.steps):
+        Ud.copy_(host_in, non_blocking=True)
+        out, st = chns.newton_step(gm, prm, opts, Ud, U1)
+        host_out.copy_(out, non_blocking=True)
+        e2e_jvp += st.jvp_calls
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e_value = dof * e2e_jvp * world / (e2e_ms * 1e-3) / 1e9
+
+    # ---- FP64 Newton step on the same problem, and the mixed step's error against it ----
+    newton = {"mixed_ms": t_ms / args.steps, "mixed_stats": stats[-1]}
+    if not args.no_fp64:
+        o64 = chns.SolverOpts.make(rtol=1e-9, atol=1e-14, krylov_rtol=1e-3, precision=0, restart=60, max_krylov=3000)
+        U64 = torch.empty_like(U0)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        _, s64 = chns.newton_step(gm, prm, o64, U0, U64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        newton.update({"fp64_ms": f0.elapsed_time(f1), "fp64_stats": s64.as_dict(),
+                       "rel_err_mixed_vs_fp64": float((U1 - U64).norm() / U64.norm()),
+                       "speedup_mixed_vs_fp64": f0.elapsed_time(f1) / (t_ms / args.steps)})
+
+    pk = peaks()
+    E = gm.E
+    jvp_avg_ms = jvp_ms / max(jvp_calls, 1)
+    hbm_bytes = 4 * dof * 4 + E * (8 * 4 + 1)      # read U^k, U^s, x; write y; e2n + level
+    roof = {"bound": "alu", "unit": "TFLOP/s", "peak": FP32_PEAK_TFLOPS,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz", "traffic": None}
+    if FLOPS_PER_ELEMENT_JVP32:
+        ach = FLOPS_PER_ELEMENT_JVP32 * E / (jvp_avg_ms * 1e-3) / 1e12
+        roof.update({"achieved": ach, "frac": ach / FP32_PEAK_TFLOPS})
+    else:
+        roof.update({"achieved": None, "frac": None})
+    hbm = {"algorithmic_bytes_per_launch": hbm_bytes, "achieved_gbs": hbm_bytes / (jvp_avg_ms * 1e-3) / 1e9,
+           "peak_gbs": pk.get("hbm_gbs"), "frac": hbm_bytes / (jvp_avg_ms * 1e-3) / 1e9 / pk.get("hbm_gbs", 6800.0),
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+    line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "elements": E, "nodes": gm.N, "dof": dof,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (GMRES basis 61 x 13.2 MB FP64 per step)"},
+            "jvp_kernel": {"avg_ms": jvp_avg_ms, "launches": jvp_calls, "gdof_s": dof / (jvp_avg_ms * 1e-3) / 1e9},
+            "roofline": roof, "hbm": hbm, "newton": newton, "clocks": clk, "gpu_launches": launches,
+            "e2e": {"value": e2e_value, "unit": "GDOF/s", "h2d_bytes_per_step": dof * 8,
+                    "d2h_bytes_per_step": dof * 8}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_oracle()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -16,9 +16,13 @@
  *  - Independent nodes are numbered in Morton (Z) order of their integer
  *    coordinates (units of the finest cell, max_level + 1 bits per axis, x fastest).
  *  - Dirichlet rows: every velocity component of every node on the boundary of
- *    the domain cube has the row R = v^{k+1} (no-slip, Definition 1).  If
- *    params.pin_pressure != 0 the pressure row of node 0 (the corner at lo^d) is
- *    R = p^{k+1} - p^k, which fixes the constant left free by closed no-slip boxes.
+ *    the domain cube has the row R = v^{k+1} (no-slip, Definition 1).
+ *  - Pressure level (closed no-slip boxes determine p only up to a constant; the
+ *    pressure rows sum to zero): params.pin_pressure = 0 keeps every row;
+ *    1 replaces the pressure row of node 0 (the corner at lo^d) by p^{k+1} - p^k
+ *    (a point value, which leaves J badly conditioned); 2 keeps every row (J has the
+ *    constant pressure as null vector) and chns_newton_step keeps
+ *    int p^{k+1} = int p^k by removing the mean of every pressure update.
  *  - Calls that take a `stream` (a cudaStream_t passed as void*, NULL = legacy
  *    default stream) are asynchronous on it, unless they return host scalars
  *    (mass, energy, Newton statistics, mu0), which synchronise that stream.
@@ -88,6 +92,8 @@ typedef struct {
 typedef struct {
     int32_t newton_its, krylov_its, jvp_calls, reason;
     double res0, res_final, du_norm;
+    double jvp_ms;       /* device time of the J x launches (CUDA events on the stream) */
+    double pc_ms;        /* device time of the preconditioner builds */
 } chns_stats;
 
 /* Build a mesh from a Morton-sorted, complete, 2:1 balanced leaf list (Section 4:
@@ -158,6 +164,10 @@ chns_status chns_energy(const chns_mesh* mesh, const chns_params* params, const 
  * relative residual of 1e-14.  Synchronises the stream. */
 chns_status chns_initial_mu(const chns_mesh* mesh, const chns_params* params, double* U_inout,
                             void* stream);
+
+/* Number of CUDA kernels this library has launched in this process (all meshes and
+ * threads), for launch accounting by callers. */
+int64_t chns_kernel_launches(void);
 
 /* Message of the last error on this thread ("" if none). */
 const char* chns_last_error(void);

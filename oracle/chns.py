@@ -34,7 +34,12 @@ Readings of the paper taken here (each also listed in the design notes):
   * Quadrature: 2-point Gauss-Legendre per axis.
   * Gravity: g_hat = -e_{d-1} (last axis); Fr <= 0 means no gravity.
   * Dirichlet rows: every velocity component of every boundary node has the row
-    R = v^{k+1}.  Pressure pin (optional): row p of node 0 is p^{k+1} - p^k.
+    R = v^{k+1}.  Pressure level (closed no-slip boxes leave p free up to a constant;
+    the pressure rows sum to zero, so one of them is redundant): pin_pressure = 1
+    replaces row p of node 0 by p^{k+1}_0 - p^k_0 (a point value: badly conditioned);
+    pin_pressure = 2 keeps every row (J then has the constant pressure as its null
+    vector) and Newton keeps int p^{k+1} = int p^k by removing the mean of each
+    pressure update.
   * No subscale time derivative (quasi-static subscales, as in Definition 2).
 """
 import math
@@ -84,7 +89,7 @@ class Params:
     """Physical and numerical parameters of one time step."""
 
     def __init__(self, dim, Re, We, Pe, Cn, Fr, rho_ratio, eta_ratio, dt, C_I=6.0, C_phi=6.0,
-                 pin_pressure=1, **_ignored):
+                 pin_pressure=2, **_ignored):
         self.dim = int(dim)
         self.Re, self.We, self.Pe, self.Cn, self.Fr = float(Re), float(We), float(Pe), float(Cn), float(Fr)
         self.rho_ratio, self.eta_ratio = float(rho_ratio), float(eta_ratio)
@@ -116,6 +121,10 @@ class Oracle:
         cx = torch.tensor(mesh.corner_x, dtype=DT)
         self.xq = torch.einsum("qa,ead->eqd", self.N, cx)
         self.detJ = (0.5 * self.h) ** d           # times unit Gauss weights
+        # integral of each independent node's basis function (hanging weights included)
+        loc = self.N.sum(0).reshape(1, -1) * self.detJ.reshape(-1, 1)        # (E, nc)
+        self.node_mass = self.scatter(loc, mesh.N)
+        self.volume = (mesh.hi - mesh.lo) ** d
 
     # -- gather / scatter with hanging-node constraints (Section 4) -------------
     def gather(self, U):
@@ -275,7 +284,7 @@ class Oracle:
         # Dirichlet rows (no-slip) and optional pressure pin
         R = R.clone()
         R[self.bnd, iv] = U_new[self.bnd, iv]
-        if prm.pin_pressure:
+        if prm.pin_pressure == 1:
             R[0, ip] = U_new[0, ip] - U_old[0, ip]
         return R
 
@@ -369,8 +378,8 @@ class Oracle:
                 cols.append(n_ * nf + f)
                 vals.append(Y[colour[n_], f, m_, g])
         ndof = U_lin.numel()
-        J = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
-                          shape=(ndof, ndof))
+        rows, cols, vals = np.concatenate(rows), np.concatenate(cols), np.concatenate(vals)
+        J = sp.csr_matrix((vals, (rows, cols)), shape=(ndof, ndof))
         J.eliminate_zeros()
         return J
 
@@ -388,7 +397,16 @@ class Oracle:
             if hist[-1] <= atol or hist[-1] <= rtol * r0:
                 break
             J = self.jacobian_sparse(prm, U_old, U)
-            dU = spla.spsolve(J.tocsc(), -R.reshape(-1).numpy())
+            if prm.pin_pressure == 2:
+                # bordered system: J dU + c lam = -R, c^T dU = 0 with c the pressure mean
+                n = U.numel()
+                c = np.zeros(n)
+                c[self.d::self.nf] = self.node_mass.numpy() / self.volume
+                K = sp.bmat([[J, sp.csr_matrix(c.reshape(-1, 1))], [sp.csr_matrix(c.reshape(1, -1)), None]])
+                rhs = np.concatenate([-R.reshape(-1).numpy(), [0.0]])
+                dU = spla.spsolve(K.tocsc(), rhs)[:n]
+            else:
+                dU = spla.spsolve(J.tocsc(), -R.reshape(-1).numpy())
             U = U + torch.tensor(dU, dtype=DT).reshape(U.shape)
             R = res(U)
             hist.append(float(torch.linalg.norm(R)))

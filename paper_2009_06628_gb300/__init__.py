@@ -11,7 +11,7 @@ import numpy as np
 import torch
 
 __all__ = ["lib", "load", "Params", "SolverOpts", "Stats", "ChnsError", "Mesh", "residual", "jvp", "vjp",
-           "newton_step", "mass", "energy", "initial_mu", "LIB_PATH"]
+           "newton_step", "mass", "energy", "initial_mu", "kernel_launches", "LIB_PATH"]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libchns.so")
 
@@ -34,7 +34,7 @@ class Params(ctypes.Structure):
                 ("C_I", ctypes.c_double), ("C_phi", ctypes.c_double)]
 
     @classmethod
-    def make(cls, dim, Re, We, Pe, Cn, Fr, rho_ratio, eta_ratio, dt, C_I=6.0, C_phi=6.0, pin_pressure=1,
+    def make(cls, dim, Re, We, Pe, Cn, Fr, rho_ratio, eta_ratio, dt, C_I=6.0, C_phi=6.0, pin_pressure=2,
              **_ignored):
         return cls(dim=dim, pin_pressure=pin_pressure, Re=Re, We=We, Pe=Pe, Cn=Cn, Fr=Fr, rho_ratio=rho_ratio,
                    eta_ratio=eta_ratio, dt=dt, C_I=C_I, C_phi=C_phi)
@@ -55,7 +55,7 @@ class SolverOpts(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("newton_its", ctypes.c_int32), ("krylov_its", ctypes.c_int32), ("jvp_calls", ctypes.c_int32),
                 ("reason", ctypes.c_int32), ("res0", ctypes.c_double), ("res_final", ctypes.c_double),
-                ("du_norm", ctypes.c_double)]
+                ("du_norm", ctypes.c_double), ("jvp_ms", ctypes.c_double), ("pc_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -81,6 +81,7 @@ SIGNATURES = [
     ("chns_mass", ctypes.c_int, [P, P, P, P]),
     ("chns_energy", ctypes.c_int, [P, P, P, P, P]),
     ("chns_initial_mu", ctypes.c_int, [P, P, P, P]),
+    ("chns_kernel_launches", ctypes.c_int64, []),
     ("chns_last_error", ctypes.c_char_p, []),
 ]
 
@@ -212,6 +213,11 @@ def energy(mesh, prm, U):
     out = (ctypes.c_double * 3)()
     _check(load().chns_energy(mesh.handle, ctypes.byref(prm), _ptr(U), out, _stream()))
     return tuple(out)
+
+
+def kernel_launches():
+    """Kernels launched by libchns so far in this process."""
+    return int(load().chns_kernel_launches())
 
 
 def initial_mu(mesh, prm, U):

@@ -1,4 +1,5 @@
 // C-ABI entry points, argument validation and error reporting.
+#include <atomic>
 #include <cmath>
 #include <string>
 
@@ -6,7 +7,12 @@
 
 namespace {
 thread_local std::string g_err;
+std::atomic<int64_t> g_launches{0};
 }
+
+void chns_count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+extern "C" int64_t chns_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 void chns_set_error(const std::string& msg) { g_err = msg; }
 

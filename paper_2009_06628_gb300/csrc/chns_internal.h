@@ -36,6 +36,8 @@ struct chns_mesh {
     uint8_t* d_nflag = nullptr;
     int32_t* d_bnodes = nullptr;
     int32_t* d_anchor = nullptr;
+    double* d_nmass = nullptr;       // integral of each node's basis function
+    double volume = 0.0;             // |Omega|
     // reduction workspace: per-block partial sums and a flag word
     double* d_partials = nullptr;
     int64_t n_partials = 0;
@@ -83,6 +85,9 @@ cudaError_t launch_dot(const chns_mesh* m, const double* a, const double* b, int
                        cudaStream_t s);
 cudaError_t launch_multidot(const chns_mesh* m, const double* V, int64_t ld, int k, const double* w, int64_t n,
                             double* out_dev, cudaStream_t s);
+
+// launch accounting (capi.cpp)
+void chns_count_launches(int n);
 
 // grid sizing helper: SM count of the current device (cached)
 int chns_num_sms();

@@ -398,7 +398,7 @@ __global__ void bc_rows_kernel(DevMesh m, const T* __restrict__ a, const T* __re
 #pragma unroll
         for (int k = 0; k < D; ++k) out[n * NF + k] = a[n * NF + k];
     }
-    if (i == 0 && pin) out[D] = b ? (a[D] - b[D]) : a[D];
+    if (i == 0 && pin == 1) out[D] = b ? (a[D] - b[D]) : a[D];
 }
 
 // ---------------------------------------------------------------------------------
@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(64) elem_vjp_kernel(DevMesh m, PCst<double> c,
             for (int f = 0; f < NF; ++f) {
                 double wv = __ldg(w + (size_t)n * NF + f);
                 if (f < D && bnd) wv = 0.0;
-                if (f == D && pin && n == 0) wv = 0.0;
+                if (f == D && pin == 1 && n == 0) wv = 0.0;
                 sw[f] += wt * wv;
             }
         }
@@ -601,7 +601,7 @@ __global__ void bc_vjp_kernel(DevMesh m, const double* __restrict__ w, double* _
 #pragma unroll
         for (int k = 0; k < D; ++k) gn[n * NF + k] += w[n * NF + k];
     }
-    if (i == 0 && pin) {
+    if (i == 0 && pin == 1) {
         gn[D] += w[D];
         if (go) go[D] -= w[D];
     }
@@ -616,15 +616,14 @@ cudaError_t launch_rj(const chns_mesh* mm, const PhysConst& pc, const T* Uo, con
     if (err != cudaSuccess) return err;
     const int EPB = Shape<D>::EPB;
     const int64_t blocks = (m.E + EPB - 1) / EPB;
-    elem_rj_kernel<D, T, MODE><<<(unsigned)blocks, EPB * Shape<D>::NC, 0, s>>>(
-        m, make_pcst<T>(pc), T(pc.inv_dt), Uo, Un, x, out, mm->d_flags);
+    { elem_rj_kernel<D, T, MODE><<<(unsigned)blocks, EPB * Shape<D>::NC, 0, s>>>( m, make_pcst<T>(pc), T(pc.inv_dt), Uo, Un, x, out, mm->d_flags); chns_count_launches(1); }
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     const int64_t nb = m.NB > 0 ? m.NB : 1;
     if (MODE == MODE_RES)
-        bc_rows_kernel<D, T><<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(m, Un, Uo, out, pin);
+        { bc_rows_kernel<D, T><<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(m, Un, Uo, out, pin); chns_count_launches(1); }
     else
-        bc_rows_kernel<D, T><<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(m, x, nullptr, out, pin);
+        { bc_rows_kernel<D, T><<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(m, x, nullptr, out, pin); chns_count_launches(1); }
     return cudaGetLastError();
 }
 
@@ -659,18 +658,16 @@ cudaError_t launch_vjp(const chns_mesh* mm, const PhysConst& pc, const double* U
     const int64_t nb = m.NB > 0 ? m.NB : 1;
     if (m.dim == 2) {
         const int EPB = 64 / 4;
-        elem_vjp_kernel<2><<<(unsigned)((m.E + EPB - 1) / EPB), 64, 0, s>>>(
-            m, make_pcst<double>(pc), pc.Cn, pc.inv_dt, U_old, U_lin, w, gU_new, gU_old, gCn, pin);
+        { elem_vjp_kernel<2><<<(unsigned)((m.E + EPB - 1) / EPB), 64, 0, s>>>( m, make_pcst<double>(pc), pc.Cn, pc.inv_dt, U_old, U_lin, w, gU_new, gU_old, gCn, pin); chns_count_launches(1); }
         err = cudaGetLastError();
         if (err != cudaSuccess) return err;
-        bc_vjp_kernel<2><<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(m, w, gU_new, gU_old, pin);
+        { bc_vjp_kernel<2><<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(m, w, gU_new, gU_old, pin); chns_count_launches(1); }
     } else {
         const int EPB = 64 / 8;
-        elem_vjp_kernel<3><<<(unsigned)((m.E + EPB - 1) / EPB), 64, 0, s>>>(
-            m, make_pcst<double>(pc), pc.Cn, pc.inv_dt, U_old, U_lin, w, gU_new, gU_old, gCn, pin);
+        { elem_vjp_kernel<3><<<(unsigned)((m.E + EPB - 1) / EPB), 64, 0, s>>>( m, make_pcst<double>(pc), pc.Cn, pc.inv_dt, U_old, U_lin, w, gU_new, gU_old, gCn, pin); chns_count_launches(1); }
         err = cudaGetLastError();
         if (err != cudaSuccess) return err;
-        bc_vjp_kernel<3><<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(m, w, gU_new, gU_old, pin);
+        { bc_vjp_kernel<3><<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(m, w, gU_new, gU_old, pin); chns_count_launches(1); }
     }
     return cudaGetLastError();
 }

@@ -2,6 +2,7 @@
 // independent-node enumeration, element-to-node map with hanging-node constraints,
 // boundary nodes, and the upload to the current CUDA device.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 
@@ -248,6 +249,24 @@ extern "C" chns_status chns_mesh_create(int32_t dim, int32_t max_level, int64_t 
             bnodes.push_back((int32_t)n);
         }
     }
+    // integral of each independent node's Q1 basis function: a corner of element e
+    // carries |e| / 2^d, shared among its parents with the constraint weights
+    std::vector<double> nmass(N, 0.0);
+    const double dom = hi - lo;
+    for (int64_t e = 0; e < E; ++e) {
+        const double h = std::ldexp(dom, -lv.level[e]);
+        const double share = (d == 2 ? h * h : h * h * h) / nc;
+        for (int c = 0; c < nc; ++c) {
+            const int32_t ent = e2n[(size_t)e * nc + c];
+            if (ent >= 0) {
+                nmass[ent] += share;
+            } else {
+                const int32_t* hp = &hang[(size_t)(-ent - 1) * 4];
+                const int np = hp[2] < 0 ? 2 : 4;
+                for (int j = 0; j < np; ++j) nmass[hp[j]] += share / np;
+            }
+        }
+    }
     std::vector<int32_t> anchor32((size_t)E * d);
     for (size_t i = 0; i < anchor32.size(); ++i) anchor32[i] = (int32_t)anchor[i];
     std::vector<int8_t> level8(E);
@@ -259,7 +278,8 @@ extern "C" chns_status chns_mesh_create(int32_t dim, int32_t max_level, int64_t 
         (st = dev_upload(&m->d_level, level8)) != CHNS_OK ||
         (st = dev_upload(&m->d_nflag, nflag)) != CHNS_OK ||
         (st = dev_upload(&m->d_bnodes, bnodes)) != CHNS_OK ||
-        (st = dev_upload(&m->d_anchor, anchor32)) != CHNS_OK) {
+        (st = dev_upload(&m->d_anchor, anchor32)) != CHNS_OK ||
+        (st = dev_upload(&m->d_nmass, nmass)) != CHNS_OK) {
         chns_mesh_destroy(m);
         return st;
     }
@@ -289,6 +309,7 @@ extern "C" chns_status chns_mesh_create(int32_t dim, int32_t max_level, int64_t 
     dm.max_level = L;
     dm.lo = lo;
     dm.hi = hi;
+    m->volume = (d == 2) ? dom * dom : dom * dom * dom;
     *out = m;
     return CHNS_OK;
 }
@@ -304,6 +325,7 @@ extern "C" void chns_mesh_destroy(chns_mesh* m) {
     cudaFree(m->d_nflag);
     cudaFree(m->d_bnodes);
     cudaFree(m->d_anchor);
+    cudaFree(m->d_nmass);
     cudaFree(m->d_partials);
     cudaFree(m->d_flags);
     if (m->h_pinned) cudaFreeHost(m->h_pinned);

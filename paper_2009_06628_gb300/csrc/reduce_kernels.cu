@@ -188,12 +188,12 @@ cudaError_t launch_mass(const chns_mesh* mm, const double* U, double* out_dev, c
     const DevMesh& m = mm->dm;
     const int nb = reduce_blocks(m.E);
     if (m.dim == 2)
-        mass_kernel<2><<<nb, 256, 0, s>>>(m, U, mm->d_partials);
+        { mass_kernel<2><<<nb, 256, 0, s>>>(m, U, mm->d_partials); chns_count_launches(1); }
     else
-        mass_kernel<3><<<nb, 256, 0, s>>>(m, U, mm->d_partials);
+        { mass_kernel<3><<<nb, 256, 0, s>>>(m, U, mm->d_partials); chns_count_launches(1); }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    final_reduce_kernel<<<1, 256, 0, s>>>(mm->d_partials, nb, 1, out_dev);
+    { final_reduce_kernel<<<1, 256, 0, s>>>(mm->d_partials, nb, 1, out_dev); chns_count_launches(1); }
     return cudaGetLastError();
 }
 
@@ -203,22 +203,22 @@ cudaError_t launch_energy(const chns_mesh* mm, const PhysConst& pc, const double
     const int nb = reduce_blocks(m.E);
     const double inv_CnWe = 1.0 / (pc.Cn * pc.We);
     if (m.dim == 2)
-        energy_kernel<2><<<nb, 256, 0, s>>>(m, pc.alpha, pc.beta, pc.Cn, inv_CnWe, pc.inv_Fr, U, mm->d_partials);
+        { energy_kernel<2><<<nb, 256, 0, s>>>(m, pc.alpha, pc.beta, pc.Cn, inv_CnWe, pc.inv_Fr, U, mm->d_partials); chns_count_launches(1); }
     else
-        energy_kernel<3><<<nb, 256, 0, s>>>(m, pc.alpha, pc.beta, pc.Cn, inv_CnWe, pc.inv_Fr, U, mm->d_partials);
+        { energy_kernel<3><<<nb, 256, 0, s>>>(m, pc.alpha, pc.beta, pc.Cn, inv_CnWe, pc.inv_Fr, U, mm->d_partials); chns_count_launches(1); }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    final_reduce_kernel<<<1, 256, 0, s>>>(mm->d_partials, nb, 3, out_dev3);
+    { final_reduce_kernel<<<1, 256, 0, s>>>(mm->d_partials, nb, 3, out_dev3); chns_count_launches(1); }
     return cudaGetLastError();
 }
 
 cudaError_t launch_dot(const chns_mesh* mm, const double* a, const double* b, int64_t n, double* out_dev,
                        cudaStream_t s) {
     const int nb = reduce_blocks(n);
-    dot_kernel<1><<<nb, 256, 0, s>>>(a, b, n, mm->d_partials);
+    { dot_kernel<1><<<nb, 256, 0, s>>>(a, b, n, mm->d_partials); chns_count_launches(1); }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    final_reduce_kernel<<<1, 256, 0, s>>>(mm->d_partials, nb, 1, out_dev);
+    { final_reduce_kernel<<<1, 256, 0, s>>>(mm->d_partials, nb, 1, out_dev); chns_count_launches(1); }
     return cudaGetLastError();
 }
 
@@ -227,10 +227,10 @@ cudaError_t launch_multidot(const chns_mesh* mm, const double* V, int64_t ld, in
     const int nb = reduce_blocks(n);
     for (int j0 = 0; j0 < k; j0 += 8) {
         const int kk = (k - j0) < 8 ? (k - j0) : 8;
-        multidot8_kernel<<<nb, 256, 0, s>>>(V + (size_t)j0 * ld, ld, kk, w, n, mm->d_partials);
+        { multidot8_kernel<<<nb, 256, 0, s>>>(V + (size_t)j0 * ld, ld, kk, w, n, mm->d_partials); chns_count_launches(1); }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        final_reduce_kernel<<<1, 256, 0, s>>>(mm->d_partials, nb, 8, out_dev + j0);
+        { final_reduce_kernel<<<1, 256, 0, s>>>(mm->d_partials, nb, 8, out_dev + j0); chns_count_launches(1); }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

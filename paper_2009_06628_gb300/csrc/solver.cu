@@ -34,6 +34,7 @@ struct SolverWS {
     double* Pinv64 = nullptr;
     double* sc = nullptr;    // device scalars
     double* hsc = nullptr;   // pinned host scalars
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // J x and preconditioner timing
 };
 
 void chns_solver_ws_free(SolverWS* ws) {
@@ -54,6 +55,8 @@ void chns_solver_ws_free(SolverWS* ws) {
     cudaFree(ws->Pinv64);
     cudaFree(ws->sc);
     if (ws->hsc) cudaFreeHost(ws->hsc);
+    for (auto& e : ws->ev)
+        if (e) cudaEventDestroy(e);
     delete ws;
 }
 
@@ -91,6 +94,8 @@ chns_status ensure_ws(chns_mesh* m, int restart) {
     A((void**)&ws->Pinv64, nb * sizeof(double));
     A((void**)&ws->sc, MAXSC * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ws->hsc, MAXSC * sizeof(double));
+    for (auto& ev : ws->ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&ev);
     if (e != cudaSuccess) {
         chns_solver_ws_free(ws);
         return chns_cuda_status(e, "cudaMalloc(solver workspace)");
@@ -335,7 +340,7 @@ __global__ void pc_invert_kernel(DevMesh m, const TB* __restrict__ blk, TI* __re
         }
     const bool bnd = m.nflag[n] & 1;
     for (int i = 0; i < NF; ++i) {
-        const bool idrow = (i < D && bnd) || (i == D && pin && n == 0);
+        const bool idrow = (i < D && bnd) || (i == D && pin == 1 && n == 0);
         if (idrow)
             for (int j = 0; j < NF; ++j) A[i][j] = (i == j) ? 1.0 : 0.0;
     }
@@ -448,6 +453,21 @@ __global__ void insert_mu_kernel(const double* __restrict__ in, int NF, int f, i
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n < N) U[(size_t)n * NF + f] = in[n];
 }
+// sum_n m_n v[n*NF + f] into per-block partials
+__global__ void field_mass_kernel(const double* __restrict__ m, const double* __restrict__ v, int NF, int f,
+                                  int64_t N, double* partials) {
+    double acc[1] = {0.0};
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
+        acc[0] += m[n] * v[(size_t)n * NF + f];
+    block_reduce_store<1>(acc, partials);
+}
+// v[n*NF + f] -= sc[0] * inv_vol
+__global__ void field_shift_kernel(double* __restrict__ v, int NF, int f, int64_t N, const double* __restrict__ sc,
+                                   double inv_vol) {
+    const double s = sc[0] * inv_vol;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
+        v[(size_t)n * NF + f] -= s;
+}
 __global__ void fill_kernel(double* __restrict__ x, double v, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         x[i] = v;
@@ -508,8 +528,7 @@ cudaError_t pc_build_launch(const chns_mesh* m, const PhysConst& pc, const T* Uo
     constexpr int NC = 1 << D, EPB = 128 / NC;
     cudaError_t e = cudaMemsetAsync(blk, 0, (size_t)m->dm.N * m->dm.nf * m->dm.nf * sizeof(T), s);
     if (e != cudaSuccess) return e;
-    pc_build_kernel<D, T><<<(unsigned)((m->dm.E + EPB - 1) / EPB), 128, 0, s>>>(m->dm, pcst_from<T>(pc),
-                                                                               T(pc.inv_dt), Uo, Un, blk);
+    { pc_build_kernel<D, T><<<(unsigned)((m->dm.E + EPB - 1) / EPB), 128, 0, s>>>(m->dm, pcst_from<T>(pc), T(pc.inv_dt), Uo, Un, blk); chns_count_launches(1); }
     return cudaGetLastError();
 }
 
@@ -540,8 +559,8 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
     S.reason = CHNS_OK;
 
     CHNS_CUDA(cudaMemsetAsync(m->d_flags, 0, sizeof(unsigned int), c.s));
-    copy64_kernel<<<c.g, 256, 0, c.s>>>(U_old, U, c.n);
-    if (mixed) to32_kernel<<<c.g, 256, 0, c.s>>>(U_old, ws->Uo32, c.n);
+    { copy64_kernel<<<c.g, 256, 0, c.s>>>(U_old, U, c.n); chns_count_launches(1); }
+    if (mixed) { to32_kernel<<<c.g, 256, 0, c.s>>>(U_old, ws->Uo32, c.n); chns_count_launches(1); }
     CHNS_CUDA(cudaGetLastError());
 
     std::vector<double> H((size_t)(mres + 1) * mres), cs(mres), sn(mres), gv(mres + 1), y(mres);
@@ -563,19 +582,22 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
         if (it >= o->max_newton) { chns_set_error("Newton did not converge"); result = CHNS_ENOCONV; break; }
 
         // linearisation state and preconditioner
+        CHNS_CUDA(cudaEventRecord(ws->ev[2], c.s));
         if (mixed) {
-            to32_kernel<<<c.g, 256, 0, c.s>>>(U, ws->Us32, c.n);
+            { to32_kernel<<<c.g, 256, 0, c.s>>>(U, ws->Us32, c.n); chns_count_launches(1); }
             cudaError_t e = (D == 2) ? pc_build_launch<2, float>(m, pc, ws->Uo32, ws->Us32, ws->Pblk32, c.s)
                                      : pc_build_launch<3, float>(m, pc, ws->Uo32, ws->Us32, ws->Pblk32, c.s);
             CHNS_CUDA(e);
-            pc_invert_kernel<float, float><<<gN, 128, 0, c.s>>>(m->dm, ws->Pblk32, ws->Pinv32, pin);
+            { pc_invert_kernel<float, float><<<gN, 128, 0, c.s>>>(m->dm, ws->Pblk32, ws->Pinv32, pin); chns_count_launches(1); }
         } else {
             cudaError_t e = (D == 2) ? pc_build_launch<2, double>(m, pc, U_old, U, ws->Pblk64, c.s)
                                      : pc_build_launch<3, double>(m, pc, U_old, U, ws->Pblk64, c.s);
             CHNS_CUDA(e);
-            pc_invert_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm, ws->Pblk64, ws->Pinv64, pin);
+            { pc_invert_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm, ws->Pblk64, ws->Pinv64, pin); chns_count_launches(1); }
         }
         CHNS_CUDA(cudaGetLastError());
+        CHNS_CUDA(cudaEventRecord(ws->ev[3], c.s));
+        bool pc_pending = true;
 
         // GMRES(mres) on J dU = -R, right preconditioned, from dU = 0
         CHNS_CUDA(cudaMemsetAsync(ws->dU, 0, c.n * sizeof(double), c.s));
@@ -583,11 +605,11 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
         double rnorm = bnorm;
         int kry = 0;
         // r = -R
-        axpby_kernel<<<c.g, 256, 0, c.s>>>(-1.0, ws->R, 0.0, ws->w, c.n);
+        { axpby_kernel<<<c.g, 256, 0, c.s>>>(-1.0, ws->R, 0.0, ws->w, c.n); chns_count_launches(1); }
         while (true) {
             // V0 = r / ||r||
             double beta = rnorm;
-            axpby_kernel<<<c.g, 256, 0, c.s>>>(1.0 / beta, ws->w, 0.0, ws->V, c.n);
+            { axpby_kernel<<<c.g, 256, 0, c.s>>>(1.0 / beta, ws->w, 0.0, ws->V, c.n); chns_count_launches(1); }
             std::fill(gv.begin(), gv.end(), 0.0);
             gv[0] = beta;
             int j = 0;
@@ -596,24 +618,38 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                 double* Vj = ws->V + (size_t)j * c.n;
                 // w = J M^{-1} V_j
                 if (mixed) {
-                    pc_apply_kernel<float, float><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv32, Vj, ws->z32);
+                    { pc_apply_kernel<float, float><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv32, Vj, ws->z32); chns_count_launches(1); }
+                    CHNS_CUDA(cudaEventRecord(ws->ev[0], c.s));
                     CHNS_CUDA(launch_jvp32(m, pc, ws->Uo32, ws->Us32, ws->z32, ws->y32, pin, c.s));
-                    to64_kernel<<<c.g, 256, 0, c.s>>>(ws->y32, ws->w, c.n);
+                    CHNS_CUDA(cudaEventRecord(ws->ev[1], c.s));
+                    { to64_kernel<<<c.g, 256, 0, c.s>>>(ws->y32, ws->w, c.n); chns_count_launches(1); }
                 } else {
-                    pc_apply_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv64, Vj, ws->z64);
+                    { pc_apply_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv64, Vj, ws->z64); chns_count_launches(1); }
+                    CHNS_CUDA(cudaEventRecord(ws->ev[0], c.s));
                     CHNS_CUDA(launch_jvp64(m, pc, U_old, U, ws->z64, ws->w, pin, c.s));
+                    CHNS_CUDA(cudaEventRecord(ws->ev[1], c.s));
                 }
                 S.jvp_calls++;
                 // classical Gram-Schmidt, twice
                 CHNS_CUDA(launch_multidot(m, ws->V, c.n, j + 1, ws->w, c.n, ws->sc, c.s));
-                gs_update_kernel<<<c.g, 256, 0, c.s>>>(ws->V, c.n, j + 1, ws->sc, ws->w, c.n);
+                { gs_update_kernel<<<c.g, 256, 0, c.s>>>(ws->V, c.n, j + 1, ws->sc, ws->w, c.n); chns_count_launches(1); }
                 CHNS_CUDA(launch_multidot(m, ws->V, c.n, j + 1, ws->w, c.n, ws->sc + 256, c.s));
-                gs_update_kernel<<<c.g, 256, 0, c.s>>>(ws->V, c.n, j + 1, ws->sc + 256, ws->w, c.n);
+                { gs_update_kernel<<<c.g, 256, 0, c.s>>>(ws->V, c.n, j + 1, ws->sc + 256, ws->w, c.n); chns_count_launches(1); }
                 CHNS_CUDA(launch_dot(m, ws->w, ws->w, c.n, ws->sc + 512, c.s));
                 double hs[2 * 256 + 1];
                 CHNS_CUDA(cudaMemcpyAsync(ws->hsc, ws->sc, 513 * sizeof(double), cudaMemcpyDeviceToHost, c.s));
                 CHNS_CUDA(cudaStreamSynchronize(c.s));
                 std::memcpy(hs, ws->hsc, 513 * sizeof(double));
+                {
+                    float ms = 0.0f;
+                    CHNS_CUDA(cudaEventElapsedTime(&ms, ws->ev[0], ws->ev[1]));
+                    S.jvp_ms += ms;
+                    if (pc_pending) {
+                        CHNS_CUDA(cudaEventElapsedTime(&ms, ws->ev[2], ws->ev[3]));
+                        S.pc_ms += ms;
+                        pc_pending = false;
+                    }
+                }
                 const double hn = std::sqrt(hs[512]);
                 for (int i = 0; i <= j; ++i) H[(size_t)i * mres + j] = hs[i] + hs[256 + i];
                 H[(size_t)(j + 1) * mres + j] = hn;
@@ -634,7 +670,7 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                 gv[j] = cs[j] * gv[j];
                 rnorm = std::fabs(gv[j + 1]);
                 if (hn > 0.0)
-                    axpby_kernel<<<c.g, 256, 0, c.s>>>(1.0 / hn, ws->w, 0.0, ws->V + (size_t)(j + 1) * c.n, c.n);
+                    { axpby_kernel<<<c.g, 256, 0, c.s>>>(1.0 / hn, ws->w, 0.0, ws->V + (size_t)(j + 1) * c.n, c.n); chns_count_launches(1); }
                 if (rnorm <= o->krylov_rtol * bnorm || hn == 0.0) {
                     ++j;
                     ++kry;
@@ -652,32 +688,50 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
             }
             std::memcpy(ws->hsc, y.data(), k * sizeof(double));
             CHNS_CUDA(cudaMemcpyAsync(ws->sc, ws->hsc, k * sizeof(double), cudaMemcpyHostToDevice, c.s));
-            combine_kernel<<<c.g, 256, 0, c.s>>>(ws->V, c.n, k, ws->sc, ws->t64, c.n);
+            { combine_kernel<<<c.g, 256, 0, c.s>>>(ws->V, c.n, k, ws->sc, ws->t64, c.n); chns_count_launches(1); }
             if (mixed)
-                pc_apply_kernel<float, double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv32, ws->t64, ws->z64);
+                { pc_apply_kernel<float, double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv32, ws->t64, ws->z64); chns_count_launches(1); }
             else
-                pc_apply_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv64, ws->t64, ws->z64);
-            axpy_kernel<<<c.g, 256, 0, c.s>>>(1.0, ws->z64, ws->dU, c.n);
+                { pc_apply_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv64, ws->t64, ws->z64); chns_count_launches(1); }
+            { axpy_kernel<<<c.g, 256, 0, c.s>>>(1.0, ws->z64, ws->dU, c.n); chns_count_launches(1); }
             CHNS_CUDA(cudaGetLastError());
             if (done || kry >= o->max_krylov) break;
             // restart: r = -R - J dU (same operator as the Arnoldi process)
             if (mixed) {
-                to32_kernel<<<c.g, 256, 0, c.s>>>(ws->dU, ws->z32, c.n);
+                { to32_kernel<<<c.g, 256, 0, c.s>>>(ws->dU, ws->z32, c.n); chns_count_launches(1); }
+                CHNS_CUDA(cudaEventRecord(ws->ev[0], c.s));
                 CHNS_CUDA(launch_jvp32(m, pc, ws->Uo32, ws->Us32, ws->z32, ws->y32, pin, c.s));
-                to64_kernel<<<c.g, 256, 0, c.s>>>(ws->y32, ws->w, c.n);
+                CHNS_CUDA(cudaEventRecord(ws->ev[1], c.s));
+                { to64_kernel<<<c.g, 256, 0, c.s>>>(ws->y32, ws->w, c.n); chns_count_launches(1); }
             } else {
+                CHNS_CUDA(cudaEventRecord(ws->ev[0], c.s));
                 CHNS_CUDA(launch_jvp64(m, pc, U_old, U, ws->dU, ws->w, pin, c.s));
+                CHNS_CUDA(cudaEventRecord(ws->ev[1], c.s));
             }
             S.jvp_calls++;
-            axpby_kernel<<<c.g, 256, 0, c.s>>>(-1.0, ws->R, -1.0, ws->w, c.n);
+            { axpby_kernel<<<c.g, 256, 0, c.s>>>(-1.0, ws->R, -1.0, ws->w, c.n); chns_count_launches(1); }
             double rr;
             if ((st = dot_host(c, ws->w, ws->w, &rr)) != CHNS_OK) return st;
             rnorm = std::sqrt(rr);
+            {
+                float ms = 0.0f;
+                CHNS_CUDA(cudaEventElapsedTime(&ms, ws->ev[0], ws->ev[1]));
+                S.jvp_ms += ms;
+            }
             if (rnorm <= o->krylov_rtol * bnorm) break;
         }
         S.krylov_its += kry;
         if (result != CHNS_OK) break;
-        axpy_kernel<<<c.g, 256, 0, c.s>>>(1.0, ws->dU, U, c.n);
+        if (pin == 2) {
+            // keep int p^{k+1} = int p^k: remove the mean of the pressure update (the
+            // constant pressure spans the null space of J when no row is pinned)
+            const int nbk = c.g < 1024 ? c.g : 1024;
+            { field_mass_kernel<<<nbk, 256, 0, c.s>>>(m->d_nmass, ws->dU, NF, D, m->dm.N, m->d_partials); chns_count_launches(1); }
+            { final_reduce_kernel<<<1, 256, 0, c.s>>>(m->d_partials, nbk, 1, ws->sc + 600); chns_count_launches(1); }
+            { field_shift_kernel<<<c.g, 256, 0, c.s>>>(ws->dU, NF, D, m->dm.N, ws->sc + 600, 1.0 / m->volume); chns_count_launches(1); }
+            CHNS_CUDA(cudaGetLastError());
+        }
+        { axpy_kernel<<<c.g, 256, 0, c.s>>>(1.0, ws->dU, U, c.n); chns_count_launches(1); }
         double du;
         if ((st = dot_host(c, ws->dU, ws->dU, &du)) != CHNS_OK) return st;
         S.du_norm = std::sqrt(du);
@@ -712,22 +766,22 @@ extern "C" chns_status chns_initial_mu(const chns_mesh* mc, const chns_params* p
     if (e == cudaSuccess) e = cudaMemsetAsync(dg, 0, N * sizeof(double), c.s);
     if (e != cudaSuccess) return chns_cuda_status(e, "cudaMemsetAsync");
     if (D == 2) {
-        mu_kernel<2, 0><<<gE, 128, 0, c.s>>>(m->dm, Cn2, U, nullptr, b);
+        { mu_kernel<2, 0><<<gE, 128, 0, c.s>>>(m->dm, Cn2, U, nullptr, b); chns_count_launches(1); }
     } else {
-        mu_kernel<3, 0><<<gE, 128, 0, c.s>>>(m->dm, Cn2, U, nullptr, b);
+        { mu_kernel<3, 0><<<gE, 128, 0, c.s>>>(m->dm, Cn2, U, nullptr, b); chns_count_launches(1); }
     }
     // Jacobi scaling by the row sums of M (the integral of each basis function, > 0)
-    fill_kernel<<<c.g, 256, 0, c.s>>>(q, 1.0, N);
+    { fill_kernel<<<c.g, 256, 0, c.s>>>(q, 1.0, N); chns_count_launches(1); }
     if (D == 2)
-        mu_kernel<2, 1><<<gE, 128, 0, c.s>>>(m->dm, Cn2, U, q, dg);
+        { mu_kernel<2, 1><<<gE, 128, 0, c.s>>>(m->dm, Cn2, U, q, dg); chns_count_launches(1); }
     else
-        mu_kernel<3, 1><<<gE, 128, 0, c.s>>>(m->dm, Cn2, U, q, dg);
+        { mu_kernel<3, 1><<<gE, 128, 0, c.s>>>(m->dm, Cn2, U, q, dg); chns_count_launches(1); }
     CHNS_CUDA(cudaGetLastError());
     // CG from x = 0
     CHNS_CUDA(cudaMemsetAsync(x, 0, N * sizeof(double), c.s));
-    copy64_kernel<<<c.g, 256, 0, c.s>>>(b, r, N);
-    jacobi_kernel<<<gN, 256, 0, c.s>>>(dg, r, z, N);
-    copy64_kernel<<<c.g, 256, 0, c.s>>>(z, pvec, N);
+    { copy64_kernel<<<c.g, 256, 0, c.s>>>(b, r, N); chns_count_launches(1); }
+    { jacobi_kernel<<<gN, 256, 0, c.s>>>(dg, r, z, N); chns_count_launches(1); }
+    { copy64_kernel<<<c.g, 256, 0, c.s>>>(z, pvec, N); chns_count_launches(1); }
     double rz, bb;
     if ((st = dot_host(c, r, z, &rz)) != CHNS_OK) return st;
     if ((st = dot_host(c, b, b, &bb)) != CHNS_OK) return st;
@@ -736,24 +790,24 @@ extern "C" chns_status chns_initial_mu(const chns_mesh* mc, const chns_params* p
     for (; it < 1000 && bb > 0.0; ++it) {
         CHNS_CUDA(cudaMemsetAsync(q, 0, N * sizeof(double), c.s));
         if (D == 2)
-            mu_kernel<2, 1><<<gE, 128, 0, c.s>>>(m->dm, Cn2, U, pvec, q);
+            { mu_kernel<2, 1><<<gE, 128, 0, c.s>>>(m->dm, Cn2, U, pvec, q); chns_count_launches(1); }
         else
-            mu_kernel<3, 1><<<gE, 128, 0, c.s>>>(m->dm, Cn2, U, pvec, q);
+            { mu_kernel<3, 1><<<gE, 128, 0, c.s>>>(m->dm, Cn2, U, pvec, q); chns_count_launches(1); }
         double pq, rr;
         if ((st = dot_host(c, pvec, q, &pq)) != CHNS_OK) return st;
         const double alpha = rz / pq;
-        axpy_kernel<<<c.g, 256, 0, c.s>>>(alpha, pvec, x, N);
-        axpy_kernel<<<c.g, 256, 0, c.s>>>(-alpha, q, r, N);
+        { axpy_kernel<<<c.g, 256, 0, c.s>>>(alpha, pvec, x, N); chns_count_launches(1); }
+        { axpy_kernel<<<c.g, 256, 0, c.s>>>(-alpha, q, r, N); chns_count_launches(1); }
         if ((st = dot_host(c, r, r, &rr)) != CHNS_OK) return st;
         if (!std::isfinite(rr)) { chns_set_error("non-finite CG residual"); return CHNS_ENAN; }
         if (std::sqrt(rr) <= tol) break;
-        jacobi_kernel<<<gN, 256, 0, c.s>>>(dg, r, z, N);
+        { jacobi_kernel<<<gN, 256, 0, c.s>>>(dg, r, z, N); chns_count_launches(1); }
         double rz2;
         if ((st = dot_host(c, r, z, &rz2)) != CHNS_OK) return st;
-        axpby_kernel<<<c.g, 256, 0, c.s>>>(1.0, z, rz2 / rz, pvec, N);
+        { axpby_kernel<<<c.g, 256, 0, c.s>>>(1.0, z, rz2 / rz, pvec, N); chns_count_launches(1); }
         rz = rz2;
     }
-    insert_mu_kernel<<<gN, 256, 0, c.s>>>(x, NF, D + 2, N, U);
+    { insert_mu_kernel<<<gN, 256, 0, c.s>>>(x, NF, D + 2, N, U); chns_count_launches(1); }
     CHNS_CUDA(cudaGetLastError());
     CHNS_CUDA(cudaStreamSynchronize(c.s));
     if (it >= 1000) { chns_set_error("mass-matrix CG did not converge"); return CHNS_ENOCONV; }

@@ -97,5 +97,5 @@ def config_params(name):
     p = dict(table[name])
     p.setdefault("C_I", 6.0)
     p.setdefault("C_phi", 6.0)
-    p.setdefault("pin_pressure", 1)
+    p.setdefault("pin_pressure", 2)
     return p

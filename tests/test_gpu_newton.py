@@ -1,0 +1,104 @@
+"""Newton step (Section 3.4) on the GPU: FP64 against the oracle's direct-solve Newton
+step, mixed precision (FP32 J x and preconditioner inside GMRES) against FP64 to
+<= 1e-9 relative, mass conservation (Proposition 1), energy decay (Theorem 1) and the
+host-side failure reports."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import Mesh as OMesh, Oracle, Params as OParams
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def chns():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_2009_06628_gb300 as chns
+    if not os.path.exists(chns.LIB_PATH):
+        from paper_2009_06628_gb300 import build
+        build.build()
+    chns.load()
+    return chns
+
+
+def drop_problem(chns, dim, leaves, max_level, cfg_name, over=None, seed=1, vmax=0.1):
+    cfg = synth.config_params(cfg_name)
+    cfg.update(over or {})
+    gm = chns.Mesh(dim, max_level, leaves)
+    x = gm.node_x()
+    U = np.zeros((gm.N, dim + 3))
+    U[:, dim + 1] = synth.drop_phi(x, [[0.5] * dim], [0.25 if dim == 2 else 0.2], cfg["Cn"], noise=1e-3, seed=seed)
+    U[:, :dim] = synth.fourier_velocity(x, 8, seed + 1, vmax)
+    bnd = np.any((x <= 0.0) | (x >= 1.0), axis=1)
+    U[bnd, :dim] = 0.0
+    Ud = torch.tensor(U, device="cuda")
+    prm = chns.Params.make(**cfg)
+    chns.initial_mu(gm, prm, Ud)
+    return gm, prm, cfg, Ud
+
+
+def test_fp64_newton_matches_oracle(chns):
+    leaves = synth.uniform_leaves(2, 5)
+    gm, prm, cfg, U0 = drop_problem(chns, 2, leaves, 5, "drop2d")
+    om = OMesh(2, 5, leaves)
+    o = Oracle(om)
+    opts = chns.SolverOpts.make(rtol=1e-12, atol=1e-16, krylov_rtol=1e-8, precision=0, restart=100,
+                                max_krylov=4000)
+    U1, st = chns.newton_step(gm, prm, opts, U0)
+    Uo, hist = o.newton_step(OParams(**cfg), U0.cpu(), rtol=1e-12, atol=1e-16)
+    err = float((U1.cpu() - Uo).norm() / Uo.norm())
+    assert err <= 1e-9, (err, st.as_dict(), hist)
+    assert st.reason == 0 and st.newton_its >= 1
+
+
+@pytest.mark.parametrize("dim,level", [(2, 6), (3, 4)])
+def test_mixed_matches_fp64(chns, dim, level):
+    leaves = synth.uniform_leaves(dim, level)
+    gm, prm, cfg, U0 = drop_problem(chns, dim, leaves, level, "drop2d" if dim == 2 else "drop3d")
+    o64 = chns.SolverOpts.make(rtol=1e-11, atol=1e-16, krylov_rtol=1e-6, precision=0)
+    o32 = chns.SolverOpts.make(rtol=1e-11, atol=1e-16, krylov_rtol=1e-4, precision=1)
+    U64, s64 = chns.newton_step(gm, prm, o64, U0)
+    U32, s32 = chns.newton_step(gm, prm, o32, U0)
+    err = float((U32 - U64).norm() / U64.norm())
+    assert err <= 1e-9, (err, s32.as_dict(), s64.as_dict())
+    # the converged mixed step has an FP64-accurate residual
+    R = chns.residual(gm, prm, U0, U32)
+    assert float(R.norm()) <= 1e-11 * s32.res0 * 1.01
+
+
+def test_adaptive_mixed_step_conserves_mass_and_energy(chns):
+    leaves = synth.sphere_band_leaves(3, 3, 6, [[0.5, 0.5, 0.5]], [0.2], 0.06)
+    gm, prm, cfg, U = drop_problem(chns, 3, leaves, 6, "drop3d", dict(rho_ratio=100.0, eta_ratio=50.0))
+    assert gm.H > 0
+    opts = chns.SolverOpts.make(rtol=1e-10, atol=1e-16, krylov_rtol=1e-4, precision=1)
+    m0 = chns.mass(gm, U)
+    e_prev = sum(chns.energy(gm, prm, U))
+    for _ in range(2):
+        U, st = chns.newton_step(gm, prm, opts, U)
+        assert st.reason == 0
+        assert abs(chns.mass(gm, U) - m0) <= 1e-12 * max(1.0, abs(m0)) + 1e-13
+        e = sum(chns.energy(gm, prm, U))
+        assert e <= e_prev + 1e-12
+        e_prev = e
+
+
+def test_newton_reports_failures_on_host(chns):
+    leaves = synth.uniform_leaves(2, 4)
+    gm, prm, cfg, U0 = drop_problem(chns, 2, leaves, 4, "drop2d")
+    opts = chns.SolverOpts.make(max_newton=0, precision=1)
+    U1, st = chns.newton_step(gm, prm, opts, U0, check=False)
+    assert st.reason == 8                      # CHNS_ENOCONV, statistics still filled
+    assert st.res0 > 0 and st.newton_its == 0
+    bad = chns.SolverOpts.make(restart=0)
+    with pytest.raises(chns.ChnsError) as e:
+        chns.newton_step(gm, prm, bad, U0)
+    assert e.value.name == "CHNS_EINVAL"
+    Unan = U0.clone()
+    Unan[3, 0] = float("nan")
+    U2, st = chns.newton_step(gm, prm, chns.SolverOpts.make(), Unan, check=False)
+    assert st.reason in (7, 10)                # CHNS_ENAN (or ETAU from the NaN radicand)

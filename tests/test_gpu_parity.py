@@ -42,11 +42,12 @@ CASES = [
     ("adaptive", 2, 6, "drop2d", dict(Fr=1.0, rho_ratio=5.0, eta_ratio=3.0)),
     ("uniform", 3, 3, "drop3d", {}),
     ("adaptive", 3, 5, "drop3d", dict(rho_ratio=100.0, eta_ratio=50.0)),
+    ("uniform", 3, 4, "drop3d", dict(pin_pressure=1)),                  # point-pinned pressure row
 ]
 
 
 def _ids(c):
-    return f"{c[0]}{c[1]}d-L{c[2]}"
+    return f"{c[0]}{c[1]}d-L{c[2]}" + ("-pin1" if c[4].get("pin_pressure") == 1 else "")
 
 
 class Case:
