@@ -79,16 +79,19 @@ typedef struct {
 
 /* Newton-Krylov options.  precision: 0 = FP64 everywhere; 1 = FP32 J.x and
  * preconditioner inside the Krylov solver, FP64 residual, orthogonalisation, dots,
- * norms and update (Newton acts as iterative refinement).  Newton stops when
- * ||R||_2 <= rtol * ||R(U^0)||_2 or ||R||_2 <= atol.  Krylov: right-preconditioned
- * GMRES(restart) with nodal block-Jacobi, relative tolerance krylov_rtol, at most
- * max_krylov iterations per Newton iteration. */
+ * norms and update (Newton acts as iterative refinement).  Norms are row-equilibrated:
+ * S = 1/|diag J| at U^0 (every field weighed by its own scale; the pressure rows carry
+ * coefficients of order tau/We).  Newton stops when ||S R||_2 <= rtol * ||S R(U^0)||_2 or
+ * ||S R||_2 <= atol.  Krylov: GMRES(restart) on S J M^{-1} (M: nodal block-Jacobi,
+ * right preconditioning) to relative tolerance krylov_rtol, at most max_krylov
+ * iterations per Newton iteration. */
 typedef struct {
     double rtol, atol, krylov_rtol;
     int32_t max_newton, max_krylov, restart, precision;
 } chns_solver_opts;
 
-/* Statistics of one Newton step (filled also on CHNS_ENOCONV / ENAN / EBREAKDOWN). */
+/* Statistics of one Newton step (filled also on CHNS_ENOCONV / ENAN / EBREAKDOWN);
+ * res0 / res_final are row-equilibrated norms ||S R||_2. */
 typedef struct {
     int32_t newton_its, krylov_its, jvp_calls, reason;
     double res0, res_final, du_norm;

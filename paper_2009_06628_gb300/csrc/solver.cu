@@ -24,6 +24,9 @@ struct SolverWS {
     double* dU = nullptr;    // n Newton update
     double* z64 = nullptr;   // n
     double* t64 = nullptr;   // n
+    double* S = nullptr;     // n row scaling 1/|diag J| of the current linearisation
+    double* S0 = nullptr;    // n row scaling of the first Newton iterate (norm of the step)
+    double* SR = nullptr;    // n scaled residual
     float* Uo32 = nullptr;   // n
     float* Us32 = nullptr;   // n
     float* z32 = nullptr;    // n
@@ -45,6 +48,9 @@ void chns_solver_ws_free(SolverWS* ws) {
     cudaFree(ws->dU);
     cudaFree(ws->z64);
     cudaFree(ws->t64);
+    cudaFree(ws->S);
+    cudaFree(ws->S0);
+    cudaFree(ws->SR);
     cudaFree(ws->Uo32);
     cudaFree(ws->Us32);
     cudaFree(ws->z32);
@@ -84,6 +90,9 @@ chns_status ensure_ws(chns_mesh* m, int restart) {
     A((void**)&ws->dU, n * sizeof(double));
     A((void**)&ws->z64, n * sizeof(double));
     A((void**)&ws->t64, n * sizeof(double));
+    A((void**)&ws->S, n * sizeof(double));
+    A((void**)&ws->S0, n * sizeof(double));
+    A((void**)&ws->SR, n * sizeof(double));
     A((void**)&ws->Uo32, n * sizeof(float));
     A((void**)&ws->Us32, n * sizeof(float));
     A((void**)&ws->z32, n * sizeof(float));
@@ -141,6 +150,13 @@ __global__ void combine_kernel(const double* __restrict__ V, int64_t ld, int k, 
         for (int j = 0; j < k; ++j) s += y[j] * V[(size_t)j * ld + i];
         u[i] = s;
     }
+}
+// y = s .* x (FP32 or FP64 x)
+template <class T>
+__global__ void scale_vec_kernel(const T* __restrict__ x, const double* __restrict__ sv, double* __restrict__ y,
+                                 int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = sv[i] * (double)x[i];
 }
 __global__ void axpy_kernel(double a, const double* __restrict__ x, double* __restrict__ y, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -328,7 +344,8 @@ __global__ void __launch_bounds__(128) pc_build_kernel(DevMesh m, PCst<T> c, T i
 // Replace Dirichlet / pin rows by identity rows and invert every block (Gauss-Jordan
 // with partial pivoting in FP64).
 template <class TB, class TI>
-__global__ void pc_invert_kernel(DevMesh m, const TB* __restrict__ blk, TI* __restrict__ inv, int pin) {
+__global__ void pc_invert_kernel(DevMesh m, const TB* __restrict__ blk, TI* __restrict__ inv, int pin,
+                                 double* __restrict__ scale) {
     const int NF = m.nf, D = m.dim;
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= m.N) return;
@@ -343,6 +360,11 @@ __global__ void pc_invert_kernel(DevMesh m, const TB* __restrict__ blk, TI* __re
         const bool idrow = (i < D && bnd) || (i == D && pin == 1 && n == 0);
         if (idrow)
             for (int j = 0; j < NF; ++j) A[i][j] = (i == j) ? 1.0 : 0.0;
+    }
+    // row equilibration 1/|J_ii| (identity rows: 1)
+    for (int i = 0; i < NF; ++i) {
+        const double a = fabs(A[i][i]);
+        scale[(size_t)n * NF + i] = a > 1e-300 ? 1.0 / a : 1.0;
     }
     for (int col = 0; col < NF; ++col) {
         int piv = col;
@@ -566,9 +588,37 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
     std::vector<double> H((size_t)(mres + 1) * mres), cs(mres), sn(mres), gv(mres + 1), y(mres);
     double r0 = 0.0, rn = 0.0;
     chns_status result = CHNS_OK;
+    auto build_pc = [&]() -> chns_status {
+        CHNS_CUDA(cudaEventRecord(ws->ev[2], c.s));
+        if (mixed) {
+            { to32_kernel<<<c.g, 256, 0, c.s>>>(U, ws->Us32, c.n); chns_count_launches(1); }
+            cudaError_t e = (D == 2) ? pc_build_launch<2, float>(m, pc, ws->Uo32, ws->Us32, ws->Pblk32, c.s)
+                                     : pc_build_launch<3, float>(m, pc, ws->Uo32, ws->Us32, ws->Pblk32, c.s);
+            CHNS_CUDA(e);
+            { pc_invert_kernel<float, float><<<gN, 128, 0, c.s>>>(m->dm, ws->Pblk32, ws->Pinv32, pin, ws->S); chns_count_launches(1); }
+        } else {
+            cudaError_t e = (D == 2) ? pc_build_launch<2, double>(m, pc, U_old, U, ws->Pblk64, c.s)
+                                     : pc_build_launch<3, double>(m, pc, U_old, U, ws->Pblk64, c.s);
+            CHNS_CUDA(e);
+            { pc_invert_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm, ws->Pblk64, ws->Pinv64, pin, ws->S); chns_count_launches(1); }
+        }
+        CHNS_CUDA(cudaGetLastError());
+        CHNS_CUDA(cudaEventRecord(ws->ev[3], c.s));
+        return CHNS_OK;
+    };
+    bool pc_pending = false;
     for (int it = 0;; ++it) {
         CHNS_CUDA(launch_residual(m, pc, U_old, U, ws->R, pin, c.s));
-        if ((st = dot_host(c, ws->R, ws->R, &rn)) != CHNS_OK) return st;
+        if (it == 0) {
+            // row equilibration of the step (1/|diag J| at U^0): the Newton test and the
+            // Krylov residual weigh every field by its own scale (the pressure rows carry
+            // coefficients ~ tau/We and would otherwise be invisible in ||R||)
+            if ((st = build_pc()) != CHNS_OK) return st;
+            pc_pending = true;
+            { copy64_kernel<<<c.g, 256, 0, c.s>>>(ws->S, ws->S0, c.n); chns_count_launches(1); }
+        }
+        { scale_vec_kernel<double><<<c.g, 256, 0, c.s>>>(ws->R, ws->S0, ws->SR, c.n); chns_count_launches(1); }
+        if ((st = dot_host(c, ws->SR, ws->SR, &rn)) != CHNS_OK) return st;
         unsigned int flag = 0;
         CHNS_CUDA(cudaMemcpy(&flag, m->d_flags, sizeof(unsigned int), cudaMemcpyDeviceToHost));
         rn = std::sqrt(rn);
@@ -581,31 +631,25 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
         if (rn <= o->atol || rn <= o->rtol * r0) break;
         if (it >= o->max_newton) { chns_set_error("Newton did not converge"); result = CHNS_ENOCONV; break; }
 
-        // linearisation state and preconditioner
-        CHNS_CUDA(cudaEventRecord(ws->ev[2], c.s));
-        if (mixed) {
-            { to32_kernel<<<c.g, 256, 0, c.s>>>(U, ws->Us32, c.n); chns_count_launches(1); }
-            cudaError_t e = (D == 2) ? pc_build_launch<2, float>(m, pc, ws->Uo32, ws->Us32, ws->Pblk32, c.s)
-                                     : pc_build_launch<3, float>(m, pc, ws->Uo32, ws->Us32, ws->Pblk32, c.s);
-            CHNS_CUDA(e);
-            { pc_invert_kernel<float, float><<<gN, 128, 0, c.s>>>(m->dm, ws->Pblk32, ws->Pinv32, pin); chns_count_launches(1); }
-        } else {
-            cudaError_t e = (D == 2) ? pc_build_launch<2, double>(m, pc, U_old, U, ws->Pblk64, c.s)
-                                     : pc_build_launch<3, double>(m, pc, U_old, U, ws->Pblk64, c.s);
-            CHNS_CUDA(e);
-            { pc_invert_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm, ws->Pblk64, ws->Pinv64, pin); chns_count_launches(1); }
+        // linearisation state and preconditioner (already built for the first iterate)
+        if (it > 0) {
+            if ((st = build_pc()) != CHNS_OK) return st;
+            pc_pending = true;
         }
-        CHNS_CUDA(cudaGetLastError());
-        CHNS_CUDA(cudaEventRecord(ws->ev[3], c.s));
-        bool pc_pending = true;
 
         // GMRES(mres) on J dU = -R, right preconditioned, from dU = 0
         CHNS_CUDA(cudaMemsetAsync(ws->dU, 0, c.n * sizeof(double), c.s));
-        const double bnorm = rn;
-        double rnorm = bnorm;
+        double rnorm = rn;
         int kry = 0;
-        // r = -R
-        { axpby_kernel<<<c.g, 256, 0, c.s>>>(-1.0, ws->R, 0.0, ws->w, c.n); chns_count_launches(1); }
+        // r = -S R (S: row equilibration of this linearisation)
+        { scale_vec_kernel<double><<<c.g, 256, 0, c.s>>>(ws->R, ws->S, ws->w, c.n); chns_count_launches(1); }
+        { axpby_kernel<<<c.g, 256, 0, c.s>>>(0.0, ws->w, -1.0, ws->w, c.n); chns_count_launches(1); }
+        {
+            double bb;
+            if ((st = dot_host(c, ws->w, ws->w, &bb)) != CHNS_OK) return st;
+            rnorm = std::sqrt(bb);
+        }
+        const double bnorm_s = rnorm;
         while (true) {
             // V0 = r / ||r||
             double beta = rnorm;
@@ -622,12 +666,13 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                     CHNS_CUDA(cudaEventRecord(ws->ev[0], c.s));
                     CHNS_CUDA(launch_jvp32(m, pc, ws->Uo32, ws->Us32, ws->z32, ws->y32, pin, c.s));
                     CHNS_CUDA(cudaEventRecord(ws->ev[1], c.s));
-                    { to64_kernel<<<c.g, 256, 0, c.s>>>(ws->y32, ws->w, c.n); chns_count_launches(1); }
+                    { scale_vec_kernel<float><<<c.g, 256, 0, c.s>>>(ws->y32, ws->S, ws->w, c.n); chns_count_launches(1); }
                 } else {
                     { pc_apply_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv64, Vj, ws->z64); chns_count_launches(1); }
                     CHNS_CUDA(cudaEventRecord(ws->ev[0], c.s));
-                    CHNS_CUDA(launch_jvp64(m, pc, U_old, U, ws->z64, ws->w, pin, c.s));
+                    CHNS_CUDA(launch_jvp64(m, pc, U_old, U, ws->z64, ws->t64, pin, c.s));
                     CHNS_CUDA(cudaEventRecord(ws->ev[1], c.s));
+                    { scale_vec_kernel<double><<<c.g, 256, 0, c.s>>>(ws->t64, ws->S, ws->w, c.n); chns_count_launches(1); }
                 }
                 S.jvp_calls++;
                 // classical Gram-Schmidt, twice
@@ -671,7 +716,7 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                 rnorm = std::fabs(gv[j + 1]);
                 if (hn > 0.0)
                     { axpby_kernel<<<c.g, 256, 0, c.s>>>(1.0 / hn, ws->w, 0.0, ws->V + (size_t)(j + 1) * c.n, c.n); chns_count_launches(1); }
-                if (rnorm <= o->krylov_rtol * bnorm || hn == 0.0) {
+                if (rnorm <= o->krylov_rtol * bnorm_s || hn == 0.0) {
                     ++j;
                     ++kry;
                     done = true;
@@ -710,6 +755,7 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
             }
             S.jvp_calls++;
             { axpby_kernel<<<c.g, 256, 0, c.s>>>(-1.0, ws->R, -1.0, ws->w, c.n); chns_count_launches(1); }
+            { scale_vec_kernel<double><<<c.g, 256, 0, c.s>>>(ws->w, ws->S, ws->w, c.n); chns_count_launches(1); }
             double rr;
             if ((st = dot_host(c, ws->w, ws->w, &rr)) != CHNS_OK) return st;
             rnorm = std::sqrt(rr);
@@ -718,7 +764,7 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                 CHNS_CUDA(cudaEventElapsedTime(&ms, ws->ev[0], ws->ev[1]));
                 S.jvp_ms += ms;
             }
-            if (rnorm <= o->krylov_rtol * bnorm) break;
+            if (rnorm <= o->krylov_rtol * bnorm_s) break;
         }
         S.krylov_its += kry;
         if (result != CHNS_OK) break;
