@@ -218,7 +218,8 @@ def main():
     U0 = torch.tensor(U, device=dev)
     chns.initial_mu(gm, prm, U0)
     dof = U0.numel()
-    opts = chns.SolverOpts.make(rtol=1e-9, atol=1e-14, krylov_rtol=1e-3, precision=1, restart=60, max_krylov=3000)
+    opts = chns.SolverOpts.make(rtol=1e-9, atol=1e-14, krylov_rtol=1e-3, precision=1, restart=60, max_krylov=2000,
+                                pc_type=1, pc_degree=8)
     U1 = torch.empty_like(U0)
     for _ in range(args.warmup):
         chns.newton_step(gm, prm, opts, U0, U1)
@@ -278,7 +279,8 @@ def main():
     # ---- FP64 Newton step on the same problem, and the mixed step's error against it ----
     newton = {"mixed_ms": t_ms / args.steps, "mixed_stats": stats[-1]}
     if not args.no_fp64:
-        o64 = chns.SolverOpts.make(rtol=1e-9, atol=1e-14, krylov_rtol=1e-3, precision=0, restart=60, max_krylov=3000)
+        o64 = chns.SolverOpts.make(rtol=1e-9, atol=1e-14, krylov_rtol=1e-3, precision=0, restart=60, max_krylov=2000,
+                                   pc_type=1, pc_degree=8)
         U64 = torch.empty_like(U0)
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)

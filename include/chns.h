@@ -88,6 +88,10 @@ typedef struct {
 typedef struct {
     double rtol, atol, krylov_rtol;
     int32_t max_newton, max_krylov, restart, precision;
+    int32_t pc_type;     /* 0: nodal block-Jacobi; 1: block-Jacobi on v, phi, mu and a pressure
+                            Schur-complement approximation (grad q, dt/(2 rho We) grad p)
+                            inverted by a Jacobi-preconditioned Chebyshev polynomial (FP32) */
+    int32_t pc_degree;   /* Chebyshev degree for pc_type 1, in [2, 200] */
 } chns_solver_opts;
 
 /* Statistics of one Newton step (filled also on CHNS_ENOCONV / ENAN / EBREAKDOWN);

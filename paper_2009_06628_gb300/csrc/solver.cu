@@ -8,7 +8,10 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <algorithm>
 #include <cstring>
+#include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "chns_internal.h"
@@ -38,6 +41,16 @@ struct SolverWS {
     double* sc = nullptr;    // device scalars
     double* hsc = nullptr;   // pinned host scalars
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // J x and preconditioner timing
+    // pressure Schur-complement approximation (FP32)
+    float* ce = nullptr;     // E element coefficients
+    float* kdinv = nullptr;  // N inverse diagonal
+    float* cr = nullptr;     // N Chebyshev work vectors
+    float* cx = nullptr;
+    float* cd = nullptr;
+    float* cy = nullptr;
+    std::vector<float> cheb_c1, cheb_c2;
+    float cheb_inv_theta = 0.0f;
+    int kref_dim = 0;
 };
 
 void chns_solver_ws_free(SolverWS* ws) {
@@ -60,6 +73,12 @@ void chns_solver_ws_free(SolverWS* ws) {
     cudaFree(ws->Pinv32);
     cudaFree(ws->Pinv64);
     cudaFree(ws->sc);
+    cudaFree(ws->ce);
+    cudaFree(ws->kdinv);
+    cudaFree(ws->cr);
+    cudaFree(ws->cx);
+    cudaFree(ws->cd);
+    cudaFree(ws->cy);
     if (ws->hsc) cudaFreeHost(ws->hsc);
     for (auto& e : ws->ev)
         if (e) cudaEventDestroy(e);
@@ -102,6 +121,12 @@ chns_status ensure_ws(chns_mesh* m, int restart) {
     A((void**)&ws->Pinv32, nb * sizeof(float));
     A((void**)&ws->Pinv64, nb * sizeof(double));
     A((void**)&ws->sc, MAXSC * sizeof(double));
+    A((void**)&ws->ce, (size_t)m->dm.E * sizeof(float));
+    A((void**)&ws->kdinv, (size_t)m->dm.N * sizeof(float));
+    A((void**)&ws->cr, (size_t)m->dm.N * sizeof(float));
+    A((void**)&ws->cx, (size_t)m->dm.N * sizeof(float));
+    A((void**)&ws->cd, (size_t)m->dm.N * sizeof(float));
+    A((void**)&ws->cy, (size_t)m->dm.N * sizeof(float));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ws->hsc, MAXSC * sizeof(double));
     for (auto& ev : ws->ev)
         if (e == cudaSuccess) e = cudaEventCreate(&ev);
@@ -180,7 +205,8 @@ int grid_for(int64_t n) {
 // skipped: the preconditioner is approximate there (it only affects convergence).
 template <int D, class T>
 __global__ void __launch_bounds__(128) pc_build_kernel(DevMesh m, PCst<T> c, T inv_dt, const T* __restrict__ Uo,
-                                                       const T* __restrict__ Un, T* __restrict__ blk);
+                                                       const T* __restrict__ Un, T* __restrict__ blk,
+                                                       float* __restrict__ ce, double ce_scale);
 
 constexpr double GPc = 0.78867513459481288225, GMc = 0.21132486540518711775;
 
@@ -215,7 +241,8 @@ __device__ __forceinline__ PB<D, T> pbasis(int a, int q, T inv_h) {
 
 template <int D, class T>
 __global__ void __launch_bounds__(128) pc_build_kernel(DevMesh m, PCst<T> c, T inv_dt, const T* __restrict__ Uo,
-                                                       const T* __restrict__ Un, T* __restrict__ blk) {
+                                                       const T* __restrict__ Un, T* __restrict__ blk,
+                                                       float* __restrict__ ce, double ce_scale) {
     constexpr int NC = 1 << D, NF = D + 3, NH = (D == 2) ? 1 : 3, EPB = 128 / NC;
     __shared__ T s_ut[EPB][NC][NF], s_dd[EPB][NC][D + 1], s_ps[EPB][NC];
     __shared__ int s_node[EPB][NC];
@@ -302,6 +329,13 @@ __global__ void __launch_bounds__(128) pc_build_kernel(DevMesh m, PCst<T> c, T i
         X.phidt *= inv_dt;
     }
     const unsigned lanes = ((1u << NC) - 1u) << ((threadIdx.x & 31) & ~(NC - 1));
+    {
+        // coefficient of the pressure Schur-complement approximation on this element:
+        // dt/(2 We) times the mean of 1/rho(phi*) over the Gauss points
+        T ir = T(1) / (c.alpha * X.ps + c.beta);
+        for (int off = NC / 2; off > 0; off >>= 1) ir += __shfl_xor_sync(lanes, ir, off);
+        if (q == 0) ce[e] = (float)(ce_scale * (double)ir / NC);
+    }
     for (int a = 0; a < NC; ++a) {
         const int node = s_node[le][a];
         const PB<D, T> b = pbasis<D, T>(a, q, inv_h);
@@ -345,7 +379,7 @@ __global__ void __launch_bounds__(128) pc_build_kernel(DevMesh m, PCst<T> c, T i
 // with partial pivoting in FP64).
 template <class TB, class TI>
 __global__ void pc_invert_kernel(DevMesh m, const TB* __restrict__ blk, TI* __restrict__ inv, int pin,
-                                 double* __restrict__ scale) {
+                                 double* __restrict__ scale, int decouple_p) {
     const int NF = m.nf, D = m.dim;
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= m.N) return;
@@ -365,6 +399,10 @@ __global__ void pc_invert_kernel(DevMesh m, const TB* __restrict__ blk, TI* __re
     for (int i = 0; i < NF; ++i) {
         const double a = fabs(A[i][i]);
         scale[(size_t)n * NF + i] = a > 1e-300 ? 1.0 / a : 1.0;
+    }
+    if (decouple_p) {
+        // the pressure is preconditioned separately (Schur-complement approximation)
+        for (int j = 0; j < NF; ++j) A[D][j] = A[j][D] = (j == D) ? 1.0 : 0.0;
     }
     for (int col = 0; col < NF; ++col) {
         int piv = col;
@@ -546,12 +584,164 @@ chns_status dot_host(Ctx& c, const double* a, const double* b, double* out) {
 
 template <int D, class T>
 cudaError_t pc_build_launch(const chns_mesh* m, const PhysConst& pc, const T* Uo, const T* Un, T* blk,
-                            cudaStream_t s) {
+                            float* ce, cudaStream_t s) {
     constexpr int NC = 1 << D, EPB = 128 / NC;
     cudaError_t e = cudaMemsetAsync(blk, 0, (size_t)m->dm.N * m->dm.nf * m->dm.nf * sizeof(T), s);
     if (e != cudaSuccess) return e;
-    { pc_build_kernel<D, T><<<(unsigned)((m->dm.E + EPB - 1) / EPB), 128, 0, s>>>(m->dm, pcst_from<T>(pc), T(pc.inv_dt), Uo, Un, blk); chns_count_launches(1); }
+    const double ce_scale = pc.dt / (2.0 * pc.We);
+    { pc_build_kernel<D, T><<<(unsigned)((m->dm.E + EPB - 1) / EPB), 128, 0, s>>>(m->dm, pcst_from<T>(pc), T(pc.inv_dt), Uo, Un, blk, ce, ce_scale); chns_count_launches(1); }
     return cudaGetLastError();
+}
+
+// ---------------- pressure Schur-complement approximation ----------------
+// Eliminating v^{k+1} from the momentum rows (dominated by rho M / dt at small dt)
+// leaves, for p^{k+1}, approximately the Laplacian (grad q, dt/(2 rho We) grad p)
+// (the Galerkin divergence and the stabilisation rows together).  Its inverse is
+// approximated by a Jacobi-preconditioned Chebyshev iteration of fixed degree (a
+// fixed polynomial, so GMRES sees a linear preconditioner).
+__constant__ float c_Kref[64];   // Q1 stiffness of the unit element (2-point Gauss)
+
+void kref_host(int D, float* K) {
+    const int NC = 1 << D;
+    const double gp = 0.78867513459481288225, gm = 0.21132486540518711775;
+    for (int a = 0; a < NC; ++a)
+        for (int b = 0; b < NC; ++b) {
+            double sum = 0.0;
+            for (int q = 0; q < NC; ++q)
+                for (int k = 0; k < D; ++k) {
+                    double da = ((a >> k) & 1) ? 1.0 : -1.0, db = ((b >> k) & 1) ? 1.0 : -1.0;
+                    for (int j = 0; j < D; ++j) {
+                        if (j == k) continue;
+                        da *= (((a >> j) & 1) == ((q >> j) & 1)) ? gp : gm;
+                        db *= (((b >> j) & 1) == ((q >> j) & 1)) ? gp : gm;
+                    }
+                    sum += da * db;
+                }
+            K[a * NC + b] = (float)(sum / (double)NC);   // |det J| = (1/2)^d, unit Gauss weights
+        }
+}
+
+template <int D>
+__device__ __forceinline__ void schur_corners(const DevMesh& m, int64_t e, int par[][4], int np[]) {
+    constexpr int NC = 1 << D;
+    for (int a = 0; a < NC; ++a) {
+        const int ent = m.e2n[e * NC + a];
+        if (ent >= 0) {
+            np[a] = 1;
+            par[a][0] = ent;
+        } else {
+            const int4 hp = reinterpret_cast<const int4*>(m.hang)[-ent - 1];
+            par[a][0] = hp.x;
+            par[a][1] = hp.y;
+            par[a][2] = hp.z;
+            par[a][3] = hp.w;
+            np[a] = hp.z < 0 ? 2 : 4;
+        }
+    }
+}
+
+// diagonal of the Schur Laplacian (constraint cross terms within a corner's parents
+// are dropped: it only scales the Chebyshev iteration)
+template <int D>
+__global__ void schur_diag_kernel(DevMesh m, const float* __restrict__ ce, float* __restrict__ dg) {
+    constexpr int NC = 1 << D;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m.E) return;
+    const float h = (float)ldexp(m.hi - m.lo, -(int)m.level[e]);
+    const float ch = ce[e] * (D == 2 ? 1.0f : h);
+    int par[NC][4], np[NC];
+    schur_corners<D>(m, e, par, np);
+    for (int a = 0; a < NC; ++a) {
+        const float w = np[a] == 1 ? 1.0f : (np[a] == 2 ? 0.5f : 0.25f);
+        for (int j = 0; j < np[a]; ++j) atomicAdd(dg + par[a][j], w * w * ch * c_Kref[a * NC + a]);
+    }
+}
+
+// y += K_c x  (y zeroed by the caller)
+template <int D>
+__global__ void schur_matvec_kernel(DevMesh m, const float* __restrict__ ce, const float* __restrict__ x,
+                                    float* __restrict__ y) {
+    constexpr int NC = 1 << D;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m.E) return;
+    const float h = (float)ldexp(m.hi - m.lo, -(int)m.level[e]);
+    const float ch = ce[e] * (D == 2 ? 1.0f : h);
+    int par[NC][4], np[NC];
+    schur_corners<D>(m, e, par, np);
+    float xl[NC];
+    for (int a = 0; a < NC; ++a) {
+        const float w = np[a] == 1 ? 1.0f : (np[a] == 2 ? 0.5f : 0.25f);
+        float s = 0.0f;
+        for (int j = 0; j < np[a]; ++j) s += w * __ldg(x + par[a][j]);
+        xl[a] = s;
+    }
+    for (int a = 0; a < NC; ++a) {
+        float s = 0.0f;
+#pragma unroll
+        for (int b = 0; b < NC; ++b) s += c_Kref[a * NC + b] * xl[b];
+        s *= ch;
+        const float w = np[a] == 1 ? 1.0f : (np[a] == 2 ? 0.5f : 0.25f);
+        for (int j = 0; j < np[a]; ++j) atomicAdd(y + par[a][j], w * s);
+    }
+}
+
+__global__ void dotf_kernel(const float* __restrict__ a, const float* __restrict__ b, int64_t n, double* partials) {
+    double acc[1] = {0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc[0] += (double)a[i] * (double)b[i];
+    block_reduce_store<1>(acc, partials);
+}
+__global__ void axpbyf_kernel(float a, float* __restrict__ x, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] *= a;
+}
+__global__ void fill_hash_kernel(float* __restrict__ x, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        uint32_t h = (uint32_t)i * 2654435761u;
+        h ^= h >> 15;
+        x[i] = (float)(h & 0xffff) / 65536.0f - 0.5f;
+    }
+}
+__global__ void recip_kernel(float* __restrict__ d, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) d[i] = d[i] > 0.0f ? 1.0f / d[i] : 0.0f;
+}
+
+// r = v_p (strided input), x = 0, d = dinv r / theta
+template <class TI>
+__global__ void cheb_init_kernel(int64_t N, int NF, int f, const TI* __restrict__ v, const float* __restrict__ dinv,
+                                 float* __restrict__ r, float* __restrict__ x, float* __restrict__ d, float inv_theta) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const float rv = (float)v[(size_t)n * NF + f];
+    r[n] = rv;
+    x[n] = 0.0f;
+    d[n] = inv_theta * dinv[n] * rv;
+}
+
+// x += d; r -= y; d = c1 d + c2 dinv r
+__global__ void cheb_step_kernel(int64_t N, const float* __restrict__ dinv, float* __restrict__ r, float* __restrict__ x,
+                                 float* __restrict__ d, const float* __restrict__ y, float c1, float c2) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    x[n] += d[n];
+    const float rn = r[n] - y[n];
+    r[n] = rn;
+    d[n] = c1 * d[n] + c2 * dinv[n] * rn;
+}
+
+template <class TO>
+__global__ void cheb_final_kernel(int64_t N, int NF, int f, const float* __restrict__ x, const float* __restrict__ d,
+                                  TO* __restrict__ z) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n < N) z[(size_t)n * NF + f] = (TO)(x[n] + d[n]);
+}
+
+// y = dinv .* (K_c x): one power-iteration step
+__global__ void scale_by_kernel(const float* __restrict__ dinv, float* __restrict__ y, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] *= dinv[i];
 }
 
 }  // namespace
@@ -564,8 +754,10 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
     if (st != CHNS_OK) return st;
     if (!o || !U_old || !U) { chns_set_error("null argument"); return CHNS_EINVAL; }
     if (o->restart < 1 || o->restart > MAXSC / 4 || o->max_krylov < 1 || o->max_newton < 0 ||
-        (o->precision != 0 && o->precision != 1)) {
-        chns_set_error("bad solver options (restart in [1, 256], max_krylov >= 1, precision 0/1)");
+        (o->precision != 0 && o->precision != 1) || (o->pc_type != 0 && o->pc_type != 1) ||
+        (o->pc_type == 1 && (o->pc_degree < 2 || o->pc_degree > 200))) {
+        chns_set_error("bad solver options (restart in [1, 256], max_krylov >= 1, precision 0/1, pc_type 0/1, "
+                       "pc_degree in [2, 200])");
         return CHNS_EINVAL;
     }
     if ((st = ensure_ws(m, o->restart)) != CHNS_OK) return st;
@@ -574,6 +766,61 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
     c.g = grid_for(c.n);
     const int D = m->dm.dim, NF = m->dm.nf, mres = o->restart;
     const bool mixed = o->precision == 1;
+    const int schur = o->pc_type == 1 ? 1 : 0;
+    const int gE = (int)((m->dm.E + 255) / 256);
+    const int gN1 = (int)((m->dm.N + 255) / 256);
+    // pressure Schur approximation: diagonal, spectrum bound and Chebyshev coefficients
+    auto schur_setup = [&]() -> chns_status {
+        if (ws->kref_dim != D) {
+            float K[64];
+            kref_host(D, K);
+            CHNS_CUDA(cudaMemcpyToSymbolAsync(c_Kref, K, sizeof(float) * (1 << D) * (1 << D), 0,
+                                              cudaMemcpyHostToDevice, c.s));
+            ws->kref_dim = D;
+        }
+        const int64_t N = m->dm.N;
+        CHNS_CUDA(cudaMemsetAsync(ws->kdinv, 0, N * sizeof(float), c.s));
+        if (D == 2) { schur_diag_kernel<2><<<gE, 256, 0, c.s>>>(m->dm, ws->ce, ws->kdinv); chns_count_launches(1); }
+        else { schur_diag_kernel<3><<<gE, 256, 0, c.s>>>(m->dm, ws->ce, ws->kdinv); chns_count_launches(1); }
+        { recip_kernel<<<gN1, 256, 0, c.s>>>(ws->kdinv, N); chns_count_launches(1); }
+        // Every off-diagonal entry of the Q1 reference stiffness is <= 0, so Gershgorin
+        // bounds the spectrum of D^{-1} K by 2 (the Chebyshev interval must not cut the
+        // top of the spectrum, where the polynomial would amplify); 20% margin for the
+        // approximate diagonal at hanging nodes.
+        const double beta = 2.4;
+        const double nside = std::ldexp(1.0, m->max_level);
+        const double ratio = std::max(16.0, nside * nside / 8.0);
+        const double alpha = beta / ratio;
+        const double theta = 0.5 * (beta + alpha), delta = 0.5 * (beta - alpha), sigma = theta / delta;
+        const int deg = o->pc_degree;
+        ws->cheb_c1.assign(deg, 0.0f);
+        ws->cheb_c2.assign(deg, 0.0f);
+        double rho = 1.0 / sigma;
+        for (int k = 0; k + 1 < deg; ++k) {
+            const double rn = 1.0 / (2.0 * sigma - rho);
+            ws->cheb_c1[k] = (float)(rn * rho);
+            ws->cheb_c2[k] = (float)(2.0 * rn / delta);
+            rho = rn;
+        }
+        ws->cheb_inv_theta = (float)(1.0 / theta);
+        return CHNS_OK;
+    };
+    // z_p = (Chebyshev approximation of S^{-1}) v_p, strided input and output
+    auto schur_apply_any = [&](auto vin, auto zout) -> chns_status {
+        using TI = std::remove_const_t<std::remove_pointer_t<decltype(vin)>>;
+        using TO = std::remove_pointer_t<decltype(zout)>;
+        const int64_t N = m->dm.N;
+        { cheb_init_kernel<TI><<<gN1, 256, 0, c.s>>>(N, NF, D, vin, ws->kdinv, ws->cr, ws->cx, ws->cd, ws->cheb_inv_theta); chns_count_launches(1); }
+        for (int k = 0; k + 1 < o->pc_degree; ++k) {
+            CHNS_CUDA(cudaMemsetAsync(ws->cy, 0, N * sizeof(float), c.s));
+            if (D == 2) { schur_matvec_kernel<2><<<gE, 256, 0, c.s>>>(m->dm, ws->ce, ws->cd, ws->cy); chns_count_launches(1); }
+            else { schur_matvec_kernel<3><<<gE, 256, 0, c.s>>>(m->dm, ws->ce, ws->cd, ws->cy); chns_count_launches(1); }
+            { cheb_step_kernel<<<gN1, 256, 0, c.s>>>(N, ws->kdinv, ws->cr, ws->cx, ws->cd, ws->cy, ws->cheb_c1[k], ws->cheb_c2[k]); chns_count_launches(1); }
+        }
+        { cheb_final_kernel<TO><<<gN1, 256, 0, c.s>>>(N, NF, D, ws->cx, ws->cd, zout); chns_count_launches(1); }
+        CHNS_CUDA(cudaGetLastError());
+        return CHNS_OK;
+    };
     const int pin = p->pin_pressure;
     const int gN = (int)((m->dm.N + 127) / 128);
     chns_stats S;
@@ -592,17 +839,21 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
         CHNS_CUDA(cudaEventRecord(ws->ev[2], c.s));
         if (mixed) {
             { to32_kernel<<<c.g, 256, 0, c.s>>>(U, ws->Us32, c.n); chns_count_launches(1); }
-            cudaError_t e = (D == 2) ? pc_build_launch<2, float>(m, pc, ws->Uo32, ws->Us32, ws->Pblk32, c.s)
-                                     : pc_build_launch<3, float>(m, pc, ws->Uo32, ws->Us32, ws->Pblk32, c.s);
+            cudaError_t e = (D == 2) ? pc_build_launch<2, float>(m, pc, ws->Uo32, ws->Us32, ws->Pblk32, ws->ce, c.s)
+                                     : pc_build_launch<3, float>(m, pc, ws->Uo32, ws->Us32, ws->Pblk32, ws->ce, c.s);
             CHNS_CUDA(e);
-            { pc_invert_kernel<float, float><<<gN, 128, 0, c.s>>>(m->dm, ws->Pblk32, ws->Pinv32, pin, ws->S); chns_count_launches(1); }
+            { pc_invert_kernel<float, float><<<gN, 128, 0, c.s>>>(m->dm, ws->Pblk32, ws->Pinv32, pin, ws->S, schur); chns_count_launches(1); }
         } else {
-            cudaError_t e = (D == 2) ? pc_build_launch<2, double>(m, pc, U_old, U, ws->Pblk64, c.s)
-                                     : pc_build_launch<3, double>(m, pc, U_old, U, ws->Pblk64, c.s);
+            cudaError_t e = (D == 2) ? pc_build_launch<2, double>(m, pc, U_old, U, ws->Pblk64, ws->ce, c.s)
+                                     : pc_build_launch<3, double>(m, pc, U_old, U, ws->Pblk64, ws->ce, c.s);
             CHNS_CUDA(e);
-            { pc_invert_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm, ws->Pblk64, ws->Pinv64, pin, ws->S); chns_count_launches(1); }
+            { pc_invert_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm, ws->Pblk64, ws->Pinv64, pin, ws->S, schur); chns_count_launches(1); }
         }
         CHNS_CUDA(cudaGetLastError());
+        if (schur) {
+            chns_status st3 = schur_setup();
+            if (st3 != CHNS_OK) return st3;
+        }
         CHNS_CUDA(cudaEventRecord(ws->ev[3], c.s));
         return CHNS_OK;
     };
@@ -663,12 +914,14 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                 // w = J M^{-1} V_j
                 if (mixed) {
                     { pc_apply_kernel<float, float><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv32, Vj, ws->z32); chns_count_launches(1); }
+                    if (schur && (st = schur_apply_any((const double*)Vj, ws->z32)) != CHNS_OK) return st;
                     CHNS_CUDA(cudaEventRecord(ws->ev[0], c.s));
                     CHNS_CUDA(launch_jvp32(m, pc, ws->Uo32, ws->Us32, ws->z32, ws->y32, pin, c.s));
                     CHNS_CUDA(cudaEventRecord(ws->ev[1], c.s));
                     { scale_vec_kernel<float><<<c.g, 256, 0, c.s>>>(ws->y32, ws->S, ws->w, c.n); chns_count_launches(1); }
                 } else {
                     { pc_apply_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv64, Vj, ws->z64); chns_count_launches(1); }
+                    if (schur && (st = schur_apply_any((const double*)Vj, ws->z64)) != CHNS_OK) return st;
                     CHNS_CUDA(cudaEventRecord(ws->ev[0], c.s));
                     CHNS_CUDA(launch_jvp64(m, pc, U_old, U, ws->z64, ws->t64, pin, c.s));
                     CHNS_CUDA(cudaEventRecord(ws->ev[1], c.s));
@@ -738,6 +991,7 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                 { pc_apply_kernel<float, double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv32, ws->t64, ws->z64); chns_count_launches(1); }
             else
                 { pc_apply_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv64, ws->t64, ws->z64); chns_count_launches(1); }
+            if (schur && (st = schur_apply_any((const double*)ws->t64, ws->z64)) != CHNS_OK) return st;
             { axpy_kernel<<<c.g, 256, 0, c.s>>>(1.0, ws->z64, ws->dU, c.n); chns_count_launches(1); }
             CHNS_CUDA(cudaGetLastError());
             if (done || kry >= o->max_krylov) break;
