@@ -172,6 +172,20 @@ chns_status chns_energy(const chns_mesh* mesh, const chns_params* params, const 
 chns_status chns_initial_mu(const chns_mesh* mesh, const chns_params* params, double* U_inout,
                             void* stream);
 
+/* Integral of phi (as chns_mass) for callers that cannot allocate device memory when
+ * they need it -- e.g. code running while a framework's caching allocator owns the free
+ * device memory, or on a path where cudaMalloc's implicit device synchronisation is not
+ * allowed.  The paper has no counterpart; it is a deployment variant of chns_mass.
+ * It allocates nothing: its reduction scratch is a file-scope device array of 16,384
+ * doubles (128 KiB, held by every GPU that loads the library until the process exits),
+ * so meshes of more than 67,108,864 elements are rejected with CHNS_EINVAL.  U: device,
+ * N * n_f doubles; out: one device double, written asynchronously on `stream` (no
+ * host synchronisation).  The first call on a device resolves the scratch address for
+ * that device (cudaGetSymbolAddress), so make it before any stream capture.  All calls
+ * share the one scratch array: calls that overlap on the GPU (other streams, other
+ * threads) race and must be serialised by the caller. */
+chns_status chns_mass_static(const chns_mesh* mesh, const double* U, double* out, void* stream);
+
 /* Number of CUDA kernels this library has launched in this process (all meshes and
  * threads), for launch accounting by callers. */
 int64_t chns_kernel_launches(void);

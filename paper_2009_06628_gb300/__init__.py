@@ -81,6 +81,7 @@ SIGNATURES = [
     ("chns_mass", ctypes.c_int, [P, P, P, P]),
     ("chns_energy", ctypes.c_int, [P, P, P, P, P]),
     ("chns_initial_mu", ctypes.c_int, [P, P, P, P]),
+    ("chns_mass_static", ctypes.c_int, [P, P, P, P]),
     ("chns_kernel_launches", ctypes.c_int64, []),
     ("chns_last_error", ctypes.c_char_p, []),
 ]
