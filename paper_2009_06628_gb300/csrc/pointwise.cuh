@@ -53,7 +53,7 @@ template <class T> __device__ __forceinline__ T value_of(Dual<T> x) { return x.v
 // Index of the mixed second derivative (i != j) in the packed array
 // (2D: xy; 3D: xy, xz, yz).
 __device__ __forceinline__ constexpr int hidx(int i, int j) {
-    return (i > j) ? hidx(j, i) : (i == 0 ? j - 1 : 2);
+    return (i < j) ? (i == 0 ? j - 1 : 2) : (j == 0 ? i - 1 : 2);
 }
 
 template <int D, class S>
