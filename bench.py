@@ -156,6 +156,18 @@ def run_reference(args, rank, world):
     return 0
 
 
+def aggregate_replicas(t_ms, work, dist=None, device="cpu"):
+    """Whole-job timing of N independent replicas: the slowest rank's time and the
+    total work of all ranks (no data-path collective; only these two reductions)."""
+    if dist is None:
+        return t_ms, work
+    t = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor([work], dtype=torch.float64, device=device)
+    dist.all_reduce(w)
+    return float(t), float(w)
+
+
 def run_profile(args):
     """One kernel of the hot path, --reps launches, on the uniform mesh of --level."""
     import paper_2009_06628_gb300 as chns
@@ -167,17 +179,29 @@ def run_profile(args):
     Un = U0 + 1e-4 * torch.randn(U0.shape, device="cuda", dtype=torch.float64,
                                  generator=torch.Generator(device="cuda").manual_seed(7))
     x = torch.randn(U0.shape, device="cuda", dtype=torch.float64, generator=torch.Generator(device="cuda").manual_seed(8))
-    for _ in range(args.reps):
+    U0f, Unf, xf = U0.float(), Un.float(), x.float()
+
+    def one():
         if args.profile == "jvp32":
-            chns.jvp(gm, prm, U0.float(), Un.float(), x.float())
+            chns.jvp(gm, prm, U0f, Unf, xf)
         elif args.profile == "jvp64":
             chns.jvp(gm, prm, U0, Un, x)
         elif args.profile == "residual":
             chns.residual(gm, prm, U0, Un)
         else:
             chns.vjp(gm, prm, U0, Un, x)
+
+    one()
     torch.cuda.synchronize()
-    print(json.dumps({"profile": args.profile, "level": args.level, "elements": gm.E, "nodes": gm.N}))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.reps):
+        one()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.reps
+    print(json.dumps({"profile": args.profile, "level": args.level, "elements": gm.E, "nodes": gm.N,
+                      "avg_ms_per_call": ms, "gdof_s": U0.numel() / (ms * 1e-3) / 1e9}))
     return 0
 
 
@@ -233,6 +257,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = chns.kernel_launches()
+    torch.cuda.nvtx.range_push("timed")
     ev0.record(stream)
     jvp_calls, jvp_ms, stats = 0, 0.0, []
     for _ in range(args.steps):
@@ -241,21 +266,13 @@ def main():
         jvp_ms += st.jvp_ms
         stats.append(st.as_dict())
     ev1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     launches = chns.kernel_launches() - launches0
     clk = clocks.stop()
-    t_ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t)
-        cnt = torch.tensor([float(jvp_calls)], device=dev)
-        dist.all_reduce(cnt)
-        total_jvp = float(cnt)
-    else:
-        total_jvp = float(jvp_calls)
+    t_ms, total_jvp = aggregate_replicas(ev0.elapsed_time(ev1), float(jvp_calls), dist, dev)
     value = dof * total_jvp / (t_ms * 1e-3) / 1e9
 
     # ---- end to end through the public API with host buffers ----

@@ -172,6 +172,36 @@ chns_status chns_energy(const chns_mesh* mesh, const chns_params* params, const 
 chns_status chns_initial_mu(const chns_mesh* mesh, const chns_params* params, double* U_inout,
                             void* stream);
 
+/* Reverse mode through one implicit step (the Newton solve of Section 3.4, Eq.
+ * newton_linear_system, transposed): for a cotangent g of U^{k+1} = U_new solving
+ * R(U_old, U_new; Cn) = 0, solve J^T lambda = P^T g by GMRES with the FP64 J^T w kernel
+ * and the transposed nodal block-Jacobi (J = dR/dU^{k+1} at (U_old, U_new); P is the
+ * pressure-level normalisation of pin mode 2), then write the cotangents
+ * gU_old = -(dR/dU^k)^T lambda (+ the normalisation's share on p^k) and
+ * *gCn = -(dR/dCn)^T lambda.  opts: restart, max_krylov, krylov_rtol are used.
+ * U_old, U_new, g, lambda, gU_old: device N * n_f doubles; gCn: device double or NULL.
+ * Synchronises the stream; CHNS_ENOCONV if GMRES stops short of krylov_rtol. */
+chns_status chns_step_adjoint(const chns_mesh* mesh, const chns_params* params, const chns_solver_opts* opts,
+                              const double* U_old, const double* U_new, const double* g, double* lambda,
+                              double* gU_old, double* gCn, chns_stats* stats, void* stream);
+
+/* Gradient of the free-energy part of E_tot (Eq. energy_functional) at one time level,
+ * F = 1/(Cn We) int psi(phi) + Cn/(2 We) int |grad phi|^2: g (device, N * n_f, only the
+ * phi field non-zero) = dF/dU, *dCn (host) = dF/dCn.  Synchronises the stream. */
+chns_status chns_free_energy_grad(const chns_mesh* mesh, const chns_params* params, const double* U, double* g,
+                                  double* dCn, void* stream);
+
+/* Reverse mode of the potential right-hand side b(phi; Cn) = (N, psi'(phi)) +
+ * Cn^2 (grad N, grad phi) that defines mu0 (chns_initial_mu): g_phi (device, N) =
+ * (db/dphi)^T lam = (N, psi''(phi) lam) + Cn^2 (grad N, grad lam), *dCn (host) =
+ * lam^T db/dCn.  U: device N * n_f (phi read), lam: device N.  Synchronises. */
+chns_status chns_mu_rhs_vjp(const chns_mesh* mesh, const chns_params* params, const double* U, const double* lam,
+                            double* g_phi, double* dCn, void* stream);
+
+/* x = M^{-1} rhs with the consistent Q1 mass matrix (CG to 1e-14; M is symmetric, so
+ * this is also its adjoint).  rhs, x: device N doubles.  Synchronises the stream. */
+chns_status chns_mass_solve(const chns_mesh* mesh, const double* rhs, double* x, void* stream);
+
 /* Integral of phi (as chns_mass) for callers that cannot allocate device memory when
  * they need it -- e.g. code running while a framework's caching allocator owns the free
  * device memory, or on a path where cudaMalloc's implicit device synchronisation is not

@@ -11,7 +11,8 @@ import numpy as np
 import torch
 
 __all__ = ["lib", "load", "Params", "SolverOpts", "Stats", "ChnsError", "Mesh", "residual", "jvp", "vjp",
-           "newton_step", "mass", "energy", "initial_mu", "kernel_launches", "LIB_PATH"]
+           "newton_step", "mass", "energy", "initial_mu", "kernel_launches", "step_adjoint", "free_energy_grad",
+           "mu_rhs_vjp", "mass_solve", "LIB_PATH"]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libchns.so")
 
@@ -82,6 +83,10 @@ SIGNATURES = [
     ("chns_energy", ctypes.c_int, [P, P, P, P, P]),
     ("chns_initial_mu", ctypes.c_int, [P, P, P, P]),
     ("chns_mass_static", ctypes.c_int, [P, P, P, P]),
+    ("chns_step_adjoint", ctypes.c_int, [P, P, P, P, P, P, P, P, P, P, P]),
+    ("chns_free_energy_grad", ctypes.c_int, [P, P, P, P, P, P]),
+    ("chns_mu_rhs_vjp", ctypes.c_int, [P, P, P, P, P, P, P]),
+    ("chns_mass_solve", ctypes.c_int, [P, P, P, P]),
     ("chns_kernel_launches", ctypes.c_int64, []),
     ("chns_last_error", ctypes.c_char_p, []),
 ]
@@ -214,6 +219,42 @@ def energy(mesh, prm, U):
     out = (ctypes.c_double * 3)()
     _check(load().chns_energy(mesh.handle, ctypes.byref(prm), _ptr(U), out, _stream()))
     return tuple(out)
+
+
+def step_adjoint(mesh, prm, opts, U_old, U_new, g, want_cn=True):
+    """Cotangents (lambda, gU_old, gCn) of one implicit step for the cotangent g of U_new."""
+    lam = torch.empty_like(g)
+    go = torch.empty_like(g)
+    gc = torch.zeros(1, dtype=torch.float64, device=g.device) if want_cn else None
+    st = Stats()
+    _check(load().chns_step_adjoint(mesh.handle, ctypes.byref(prm), ctypes.byref(opts), _ptr(U_old), _ptr(U_new),
+                                    _ptr(g), _ptr(lam), _ptr(go), _ptr(gc) if gc is not None else None,
+                                    ctypes.byref(st), _stream()))
+    return lam, go, gc, st
+
+
+def free_energy_grad(mesh, prm, U):
+    """(dF/dU, dF/dCn) of the free-energy part F of E_tot."""
+    g = torch.empty_like(U)
+    d = ctypes.c_double()
+    _check(load().chns_free_energy_grad(mesh.handle, ctypes.byref(prm), _ptr(U), _ptr(g), ctypes.byref(d),
+                                        _stream()))
+    return g, d.value
+
+
+def mu_rhs_vjp(mesh, prm, U, lam):
+    """((db/dphi)^T lam, lam^T db/dCn) of the potential right-hand side b(phi; Cn)."""
+    g = torch.empty(U.shape[0], dtype=torch.float64, device=U.device)
+    d = ctypes.c_double()
+    _check(load().chns_mu_rhs_vjp(mesh.handle, ctypes.byref(prm), _ptr(U), _ptr(lam.contiguous()), _ptr(g),
+                                  ctypes.byref(d), _stream()))
+    return g, d.value
+
+
+def mass_solve(mesh, rhs):
+    x = torch.empty_like(rhs)
+    _check(load().chns_mass_solve(mesh.handle, _ptr(rhs.contiguous()), _ptr(x), _stream()))
+    return x
 
 
 def kernel_launches():

@@ -70,10 +70,10 @@ __device__ __forceinline__ Basis<D, T> basis(int a, int q, T inv_h) {
 template <class T>
 __device__ __forceinline__ T clip1(T x) { return x > T(1) ? T(1) : (x < T(-1) ? T(-1) : x); }
 
-template <class T>
-__device__ __forceinline__ T phys_h(const DevMesh& m, int lev) {
-    return T(ldexp(m.hi - m.lo, -lev));
-}
+// element size (hi - lo) 2^-level, exact in the working precision (no FP64 work in
+// the FP32 kernels: GB300's FP64 pipe is 1/64 of its FP32 rate)
+__device__ __forceinline__ float scale_pow2(float span, int lev) { return ldexpf(span, -lev); }
+__device__ __forceinline__ double scale_pow2(double span, int lev) { return ldexp(span, -lev); }
 
 // Corner parents and weights of element corner entry `ent`.
 struct Parents {
@@ -258,7 +258,8 @@ struct SmemRJ {
 };
 
 template <int D, class T, int MODE>
-__global__ void __launch_bounds__(128) elem_rj_kernel(DevMesh m, PCst<T> c, T inv_dt,
+__global__ void __launch_bounds__(128, (MODE == MODE_JVP && sizeof(T) == 4) ? 5 : 1)
+elem_rj_kernel(DevMesh m, PCst<T> c, T inv_dt, T span,
                                                       const T* __restrict__ Uo,
                                                       const T* __restrict__ Un,
                                                       const T* __restrict__ xin, T* __restrict__ out,
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(128) elem_rj_kernel(DevMesh m, PCst<T> c, T in
         const int ent = m.e2n[e * NC + t];
         P = parents_of(m, ent);
         const unsigned mask = gather_primal<D, T>(m, P, Uo, Un, S.cp, t);
-        const T h = phys_h<T>(m, m.level[e]);
+        const T h = scale_pow2(span, (int)m.level[e]);
         inv_h = T(1) / h;
         detJ = (D == 2) ? (T(0.25) * h * h) : (T(0.125) * h * h * h);
         if (MODE == MODE_JVP) {
@@ -437,7 +438,7 @@ __global__ void __launch_bounds__(64) elem_vjp_kernel(DevMesh m, PCst<double> c,
     if (valid) {
         P = parents_of(m, m.e2n[e * NC + t]);
         mask = gather_primal<D, double>(m, P, Uo, Un, S.cp, t);
-        const double h = phys_h<double>(m, m.level[e]);
+        const double h = scale_pow2(m.hi - m.lo, (int)m.level[e]);
         inv_h = 1.0 / h;
         detJ = (D == 2) ? 0.25 * h * h : 0.125 * h * h * h;
         // adjoint seed: w on rows that the element contributes to (Dirichlet and pin
@@ -616,7 +617,7 @@ cudaError_t launch_rj(const chns_mesh* mm, const PhysConst& pc, const T* Uo, con
     if (err != cudaSuccess) return err;
     const int EPB = Shape<D>::EPB;
     const int64_t blocks = (m.E + EPB - 1) / EPB;
-    { elem_rj_kernel<D, T, MODE><<<(unsigned)blocks, EPB * Shape<D>::NC, 0, s>>>( m, make_pcst<T>(pc), T(pc.inv_dt), Uo, Un, x, out, mm->d_flags); chns_count_launches(1); }
+    { elem_rj_kernel<D, T, MODE><<<(unsigned)blocks, EPB * Shape<D>::NC, 0, s>>>( m, make_pcst<T>(pc), T(pc.inv_dt), T(m.hi - m.lo), Uo, Un, x, out, mm->d_flags); chns_count_launches(1); }
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     const int64_t nb = m.NB > 0 ? m.NB : 1;

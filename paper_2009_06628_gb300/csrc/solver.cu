@@ -48,6 +48,7 @@ struct SolverWS {
     float* cx = nullptr;
     float* cd = nullptr;
     float* cy = nullptr;
+    double* part = nullptr;  // per-block partials of the fused orthogonalisation reductions
     std::vector<float> cheb_c1, cheb_c2;
     float cheb_inv_theta = 0.0f;
     int kref_dim = 0;
@@ -79,6 +80,7 @@ void chns_solver_ws_free(SolverWS* ws) {
     cudaFree(ws->cx);
     cudaFree(ws->cd);
     cudaFree(ws->cy);
+    cudaFree(ws->part);
     if (ws->hsc) cudaFreeHost(ws->hsc);
     for (auto& e : ws->ev)
         if (e) cudaEventDestroy(e);
@@ -88,6 +90,7 @@ void chns_solver_ws_free(SolverWS* ws) {
 namespace {
 
 constexpr int MAXSC = 1024;
+constexpr int ORTH_MAX_BX = 1024;   // row blocks of the fused orthogonalisation kernels
 
 chns_status ensure_ws(chns_mesh* m, int restart) {
     SolverWS* ws = m->ws;
@@ -127,6 +130,7 @@ chns_status ensure_ws(chns_mesh* m, int restart) {
     A((void**)&ws->cx, (size_t)m->dm.N * sizeof(float));
     A((void**)&ws->cd, (size_t)m->dm.N * sizeof(float));
     A((void**)&ws->cy, (size_t)m->dm.N * sizeof(float));
+    A((void**)&ws->part, (size_t)ORTH_MAX_BX * (MAXSC / 32 + 1) * 9 * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ws->hsc, MAXSC * sizeof(double));
     for (auto& ev : ws->ev)
         if (e == cudaSuccess) e = cudaEventCreate(&ev);
@@ -166,6 +170,71 @@ __global__ void gs_update_kernel(const double* __restrict__ V, int64_t ld, int k
         for (int j = 0; j < k; ++j) s -= h[j] * V[(size_t)j * ld + i];
         w[i] = s;
     }
+}
+// Fused h = V^T w for all k basis vectors (blockIdx.y picks 8 of them) and, in chunk 0,
+// also w . w: partials[(chunk * gridDim.x + block) * 9 + j].
+__global__ void orth_dots_kernel(const double* __restrict__ V, int64_t ld, int k, const double* __restrict__ w,
+                                 int64_t n, double* __restrict__ partials) {
+    const int chunk = blockIdx.y;
+    const int j0 = chunk * 8;
+    const int kk = min(8, k - j0);
+    double acc[9];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) acc[j] = 0.0;
+    const double* Vc = V + (size_t)j0 * ld;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double wi = w[i];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < kk) acc[j] += Vc[(size_t)j * ld + i] * wi;
+        if (chunk == 0) acc[8] += wi * wi;
+    }
+    // block reduction of 9 values
+    __shared__ double sred[32][9];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        double v = acc[j];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) sred[warp][j] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 9) {
+        double v = 0.0;
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) v += sred[w2][threadIdx.x];
+        partials[((size_t)chunk * gridDim.x + blockIdx.x) * 9 + threadIdx.x] = v;
+    }
+}
+// out[j] = sum over row blocks (one block per chunk, one warp per value), out_norm = w.w
+__global__ void orth_dots_final_kernel(const double* __restrict__ partials, int nbx, int k, double* __restrict__ out,
+                                       double* __restrict__ out_norm) {
+    const int chunk = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;   // 9 warps
+    const int j = warp;
+    if (j >= 9) return;
+    if (j < 8 && chunk * 8 + j >= k) return;
+    if (j == 8 && chunk != 0) return;
+    double v = 0.0;
+    for (int b = lane; b < nbx; b += 32) v += partials[((size_t)chunk * nbx + b) * 9 + j];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) {
+        if (j < 8) out[chunk * 8 + j] = v;
+        else out_norm[0] = v;
+    }
+}
+// w -= sum_{j<k} h[j] V_j, and per-block partials of the new w . w
+__global__ void gs_update_norm_kernel(const double* __restrict__ V, int64_t ld, int k, const double* __restrict__ h,
+                                      double* __restrict__ w, int64_t n, double* __restrict__ partials) {
+    double acc[1] = {0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = w[i];
+        for (int j = 0; j < k; ++j) s -= h[j] * V[(size_t)j * ld + i];
+        w[i] = s;
+        acc[0] += s * s;
+    }
+    block_reduce_store<1>(acc, partials);
 }
 // u = sum_{j<k} y[j] V_j (y host-provided via device scalars)
 __global__ void combine_kernel(const double* __restrict__ V, int64_t ld, int k, const double* __restrict__ y,
@@ -835,6 +904,18 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
     std::vector<double> H((size_t)(mres + 1) * mres), cs(mres), sn(mres), gv(mres + 1), y(mres);
     double r0 = 0.0, rn = 0.0;
     chns_status result = CHNS_OK;
+    // one classical Gram-Schmidt pass against V_0..V_{k-1}: h -> hdev[0..k), |w|^2 before
+    // -> nrm_before, |w|^2 after -> nrm_after (all device scalars)
+    auto orth_pass = [&](int k, double* hdev, double* nrm_before, double* nrm_after) -> chns_status {
+        int nbx = c.g < ORTH_MAX_BX ? c.g : ORTH_MAX_BX;
+        const int nch = (k + 7) / 8;
+        { orth_dots_kernel<<<dim3(nbx, nch), 256, 0, c.s>>>(ws->V, c.n, k, ws->w, c.n, ws->part); chns_count_launches(1); }
+        { orth_dots_final_kernel<<<nch, 288, 0, c.s>>>(ws->part, nbx, k, hdev, nrm_before); chns_count_launches(1); }
+        { gs_update_norm_kernel<<<nbx, 256, 0, c.s>>>(ws->V, c.n, k, hdev, ws->w, c.n, m->d_partials); chns_count_launches(1); }
+        { final_reduce_kernel<<<1, 256, 0, c.s>>>(m->d_partials, nbx, 1, nrm_after); chns_count_launches(1); }
+        CHNS_CUDA(cudaGetLastError());
+        return CHNS_OK;
+    };
     auto build_pc = [&]() -> chns_status {
         CHNS_CUDA(cudaEventRecord(ws->ev[2], c.s));
         if (mixed) {
@@ -928,16 +1009,28 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                     { scale_vec_kernel<double><<<c.g, 256, 0, c.s>>>(ws->t64, ws->S, ws->w, c.n); chns_count_launches(1); }
                 }
                 S.jvp_calls++;
-                // classical Gram-Schmidt, twice
-                CHNS_CUDA(launch_multidot(m, ws->V, c.n, j + 1, ws->w, c.n, ws->sc, c.s));
-                { gs_update_kernel<<<c.g, 256, 0, c.s>>>(ws->V, c.n, j + 1, ws->sc, ws->w, c.n); chns_count_launches(1); }
-                CHNS_CUDA(launch_multidot(m, ws->V, c.n, j + 1, ws->w, c.n, ws->sc + 256, c.s));
-                { gs_update_kernel<<<c.g, 256, 0, c.s>>>(ws->V, c.n, j + 1, ws->sc + 256, ws->w, c.n); chns_count_launches(1); }
-                CHNS_CUDA(launch_dot(m, ws->w, ws->w, c.n, ws->sc + 512, c.s));
+                // classical Gram-Schmidt with selective re-orthogonalisation (DGKS: a
+                // second pass only when the first removed more than 1 - 1/sqrt(2) of |w|)
                 double hs[2 * 256 + 1];
-                CHNS_CUDA(cudaMemcpyAsync(ws->hsc, ws->sc, 513 * sizeof(double), cudaMemcpyDeviceToHost, c.s));
-                CHNS_CUDA(cudaStreamSynchronize(c.s));
-                std::memcpy(hs, ws->hsc, 513 * sizeof(double));
+                for (int i = 0; i <= j; ++i) hs[256 + i] = 0.0;
+                {
+                    chns_status so = orth_pass(j + 1, ws->sc, ws->sc + 600, ws->sc + 601);
+                    if (so != CHNS_OK) return so;
+                    CHNS_CUDA(cudaMemcpyAsync(ws->hsc, ws->sc, 602 * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+                    CHNS_CUDA(cudaStreamSynchronize(c.s));
+                    for (int i = 0; i <= j; ++i) hs[i] = ws->hsc[i];
+                    double w2 = ws->hsc[600], wn2 = ws->hsc[601];
+                    if (wn2 < 0.5 * w2) {
+                        so = orth_pass(j + 1, ws->sc + 256, ws->sc + 602, ws->sc + 603);
+                        if (so != CHNS_OK) return so;
+                        CHNS_CUDA(cudaMemcpyAsync(ws->hsc + 256, ws->sc + 256, 348 * sizeof(double),
+                                                  cudaMemcpyDeviceToHost, c.s));
+                        CHNS_CUDA(cudaStreamSynchronize(c.s));
+                        for (int i = 0; i <= j; ++i) hs[256 + i] = ws->hsc[256 + i];
+                        wn2 = ws->hsc[603];
+                    }
+                    hs[512] = wn2;
+                }
                 {
                     float ms = 0.0f;
                     CHNS_CUDA(cudaEventElapsedTime(&ms, ws->ev[0], ws->ev[1]));
@@ -1108,6 +1201,242 @@ extern "C" chns_status chns_initial_mu(const chns_mesh* mc, const chns_params* p
         rz = rz2;
     }
     { insert_mu_kernel<<<gN, 256, 0, c.s>>>(x, NF, D + 2, N, U); chns_count_launches(1); }
+    CHNS_CUDA(cudaGetLastError());
+    CHNS_CUDA(cudaStreamSynchronize(c.s));
+    if (it >= 1000) { chns_set_error("mass-matrix CG did not converge"); return CHNS_ENOCONV; }
+    return CHNS_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Adjoint of one implicit step (reverse mode through Section 3.4's solve): with
+// R(U^k, U^{k+1}; Cn) = 0, a cotangent g of U^{k+1} gives J^T lambda = P^T g
+// (J = dR/dU^{k+1}; P the pressure-level normalisation of pin mode 2) and the
+// cotangents -(dR/dU^k)^T lambda of U^k and -(dR/dCn)^T lambda of Cn.
+// ---------------------------------------------------------------------------------
+namespace {
+
+template <class TI>
+__global__ void pc_apply_T_kernel(int64_t N, int NF, const TI* __restrict__ inv, const double* __restrict__ v,
+                                  double* __restrict__ z) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    double x[6];
+    for (int j = 0; j < NF; ++j) x[j] = v[(size_t)n * NF + j];
+    for (int i = 0; i < NF; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < NF; ++j) s += (double)inv[((size_t)n * NF + j) * NF + i] * x[j];
+        z[(size_t)n * NF + i] = s;
+    }
+}
+
+// unweighted sum of field f into per-block partials
+__global__ void field_sum_kernel(const double* __restrict__ v, int NF, int f, int64_t N, double* partials) {
+    double acc[1] = {0.0};
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
+        acc[0] += v[(size_t)n * NF + f];
+    block_reduce_store<1>(acc, partials);
+}
+// v[n*NF + f] += a * m[n] * sc[0]
+__global__ void field_axpy_mass_kernel(double* __restrict__ v, int NF, int f, int64_t N, const double* __restrict__ m,
+                                       const double* __restrict__ sc, double a) {
+    const double s = a * sc[0];
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
+        v[(size_t)n * NF + f] += s * m[n];
+}
+
+}  // namespace
+
+extern "C" chns_status chns_step_adjoint(const chns_mesh* mc, const chns_params* p, const chns_solver_opts* o,
+                                         const double* U_old, const double* U_new, const double* g, double* lambda,
+                                         double* gU_old, double* gCn, chns_stats* stats, void* stream) {
+    chns_mesh* m = const_cast<chns_mesh*>(mc);
+    PhysConst pc;
+    chns_status st = chns_check_params(mc, p, &pc);
+    if (st != CHNS_OK) return st;
+    if (!o || !U_old || !U_new || !g || !lambda || !gU_old) { chns_set_error("null argument"); return CHNS_EINVAL; }
+    if (o->restart < 1 || o->restart > MAXSC / 4 || o->max_krylov < 1) {
+        chns_set_error("bad solver options (restart in [1, 256], max_krylov >= 1)");
+        return CHNS_EINVAL;
+    }
+    if ((st = ensure_ws(m, o->restart)) != CHNS_OK) return st;
+    SolverWS* ws = m->ws;
+    Ctx c{m, ws, (cudaStream_t)stream, ws->n, 0};
+    c.g = grid_for(c.n);
+    const int D = m->dm.dim, NF = m->dm.nf, mres = o->restart, pin = p->pin_pressure;
+    const int gN = (int)((m->dm.N + 127) / 128);
+    const int nbk = c.g < 1024 ? c.g : 1024;
+    chns_stats S;
+    std::memset(&S, 0, sizeof(S));
+
+    // nodal blocks of J (FP64) at the converged state; J^T's blocks are their transposes
+    cudaError_t ce = (D == 2) ? pc_build_launch<2, double>(m, pc, U_old, U_new, ws->Pblk64, ws->ce, c.s)
+                              : pc_build_launch<3, double>(m, pc, U_old, U_new, ws->Pblk64, ws->ce, c.s);
+    CHNS_CUDA(ce);
+    { pc_invert_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm, ws->Pblk64, ws->Pinv64, pin, ws->S, 0); chns_count_launches(1); }
+    // b = P^T g: remove sum(g_p) * m / |Omega| from the pressure part (pin mode 2)
+    double* b = ws->R;
+    { copy64_kernel<<<c.g, 256, 0, c.s>>>(g, b, c.n); chns_count_launches(1); }
+    if (pin == 2) {
+        { field_sum_kernel<<<nbk, 256, 0, c.s>>>(g, NF, D, m->dm.N, m->d_partials); chns_count_launches(1); }
+        { final_reduce_kernel<<<1, 256, 0, c.s>>>(m->d_partials, nbk, 1, ws->sc + 800); chns_count_launches(1); }
+        { field_axpy_mass_kernel<<<c.g, 256, 0, c.s>>>(b, NF, D, m->dm.N, m->d_nmass, ws->sc + 800, -1.0 / m->volume); chns_count_launches(1); }
+    }
+    CHNS_CUDA(cudaGetLastError());
+    double bb;
+    if ((st = dot_host(c, b, b, &bb)) != CHNS_OK) return st;
+    const double bnorm = std::sqrt(bb);
+    CHNS_CUDA(cudaMemsetAsync(lambda, 0, c.n * sizeof(double), c.s));
+    S.res0 = bnorm;
+    chns_status result = CHNS_OK;
+    if (bnorm > 0.0) {
+        // right-preconditioned GMRES on J^T M^{-T} y = b, lambda = M^{-T} y
+        std::vector<double> H((size_t)(mres + 1) * mres), cs(mres), sn(mres), gv(mres + 1), y(mres);
+        double rnorm = bnorm;
+        int kry = 0;
+        { copy64_kernel<<<c.g, 256, 0, c.s>>>(b, ws->w, c.n); chns_count_launches(1); }
+        while (true) {
+            const double beta = rnorm;
+            { axpby_kernel<<<c.g, 256, 0, c.s>>>(1.0 / beta, ws->w, 0.0, ws->V, c.n); chns_count_launches(1); }
+            std::fill(gv.begin(), gv.end(), 0.0);
+            gv[0] = beta;
+            int j = 0;
+            bool done = false;
+            for (; j < mres && kry < o->max_krylov; ++j, ++kry) {
+                double* Vj = ws->V + (size_t)j * c.n;
+                { pc_apply_T_kernel<double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv64, Vj, ws->z64); chns_count_launches(1); }
+                CHNS_CUDA(launch_vjp(m, pc, U_old, U_new, ws->z64, ws->w, nullptr, nullptr, pin, c.s));
+                S.jvp_calls++;
+                CHNS_CUDA(launch_multidot(m, ws->V, c.n, j + 1, ws->w, c.n, ws->sc, c.s));
+                { gs_update_kernel<<<c.g, 256, 0, c.s>>>(ws->V, c.n, j + 1, ws->sc, ws->w, c.n); chns_count_launches(1); }
+                CHNS_CUDA(launch_multidot(m, ws->V, c.n, j + 1, ws->w, c.n, ws->sc + 256, c.s));
+                { gs_update_kernel<<<c.g, 256, 0, c.s>>>(ws->V, c.n, j + 1, ws->sc + 256, ws->w, c.n); chns_count_launches(1); }
+                CHNS_CUDA(launch_dot(m, ws->w, ws->w, c.n, ws->sc + 512, c.s));
+                double hs[513];
+                CHNS_CUDA(cudaMemcpyAsync(ws->hsc, ws->sc, 513 * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+                CHNS_CUDA(cudaStreamSynchronize(c.s));
+                std::memcpy(hs, ws->hsc, 513 * sizeof(double));
+                const double hn = std::sqrt(hs[512]);
+                for (int i = 0; i <= j; ++i) H[(size_t)i * mres + j] = hs[i] + hs[256 + i];
+                H[(size_t)(j + 1) * mres + j] = hn;
+                if (!std::isfinite(hn)) { chns_set_error("non-finite Arnoldi vector"); result = CHNS_EBREAKDOWN; break; }
+                for (int i = 0; i < j; ++i) {
+                    const double a = H[(size_t)i * mres + j], bq = H[(size_t)(i + 1) * mres + j];
+                    H[(size_t)i * mres + j] = cs[i] * a + sn[i] * bq;
+                    H[(size_t)(i + 1) * mres + j] = -sn[i] * a + cs[i] * bq;
+                }
+                const double a = H[(size_t)j * mres + j], bq = H[(size_t)(j + 1) * mres + j];
+                const double r = std::hypot(a, bq);
+                cs[j] = r > 0 ? a / r : 1.0;
+                sn[j] = r > 0 ? bq / r : 0.0;
+                H[(size_t)j * mres + j] = r;
+                H[(size_t)(j + 1) * mres + j] = 0.0;
+                gv[j + 1] = -sn[j] * gv[j];
+                gv[j] = cs[j] * gv[j];
+                rnorm = std::fabs(gv[j + 1]);
+                if (hn > 0.0)
+                    { axpby_kernel<<<c.g, 256, 0, c.s>>>(1.0 / hn, ws->w, 0.0, ws->V + (size_t)(j + 1) * c.n, c.n); chns_count_launches(1); }
+                if (rnorm <= o->krylov_rtol * bnorm || hn == 0.0) {
+                    ++j;
+                    ++kry;
+                    done = true;
+                    break;
+                }
+            }
+            if (result != CHNS_OK) break;
+            const int k = j;
+            for (int i = k - 1; i >= 0; --i) {
+                double sacc = gv[i];
+                for (int l = i + 1; l < k; ++l) sacc -= H[(size_t)i * mres + l] * y[l];
+                y[i] = sacc / H[(size_t)i * mres + i];
+            }
+            std::memcpy(ws->hsc, y.data(), k * sizeof(double));
+            CHNS_CUDA(cudaMemcpyAsync(ws->sc, ws->hsc, k * sizeof(double), cudaMemcpyHostToDevice, c.s));
+            { combine_kernel<<<c.g, 256, 0, c.s>>>(ws->V, c.n, k, ws->sc, ws->t64, c.n); chns_count_launches(1); }
+            { pc_apply_T_kernel<double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv64, ws->t64, ws->z64); chns_count_launches(1); }
+            { axpy_kernel<<<c.g, 256, 0, c.s>>>(1.0, ws->z64, lambda, c.n); chns_count_launches(1); }
+            CHNS_CUDA(cudaGetLastError());
+            if (done || kry >= o->max_krylov) break;
+            // restart: r = b - J^T lambda
+            CHNS_CUDA(launch_vjp(m, pc, U_old, U_new, lambda, ws->w, nullptr, nullptr, pin, c.s));
+            S.jvp_calls++;
+            { axpby_kernel<<<c.g, 256, 0, c.s>>>(1.0, b, -1.0, ws->w, c.n); chns_count_launches(1); }
+            double rr;
+            if ((st = dot_host(c, ws->w, ws->w, &rr)) != CHNS_OK) return st;
+            rnorm = std::sqrt(rr);
+            if (rnorm <= o->krylov_rtol * bnorm) break;
+        }
+        S.krylov_its = kry;
+        S.res_final = rnorm;
+        if (result == CHNS_OK && rnorm > o->krylov_rtol * bnorm * 1.0001) {
+            chns_set_error("adjoint GMRES did not reach krylov_rtol within max_krylov");
+            result = CHNS_ENOCONV;
+        }
+    }
+    // cotangents of U^k and Cn: -(dR/dU^k)^T lambda, -(dR/dCn)^T lambda
+    CHNS_CUDA(launch_vjp(m, pc, U_old, U_new, lambda, ws->t64, gU_old, gCn, pin, c.s));
+    { axpby_kernel<<<c.g, 256, 0, c.s>>>(0.0, gU_old, -1.0, gU_old, c.n); chns_count_launches(1); }
+    if (gCn) { axpby_kernel<<<1, 32, 0, c.s>>>(0.0, gCn, -1.0, gCn, 1); chns_count_launches(1); }
+    if (pin == 2) {
+        // the normalisation int p^{k+1} = int p^k passes sum(g_p) m / |Omega| to p^k
+        { field_axpy_mass_kernel<<<c.g, 256, 0, c.s>>>(gU_old, NF, D, m->dm.N, m->d_nmass, ws->sc + 800, 1.0 / m->volume); chns_count_launches(1); }
+    }
+    CHNS_CUDA(cudaGetLastError());
+    CHNS_CUDA(cudaStreamSynchronize(c.s));
+    S.reason = result;
+    if (stats) *stats = S;
+    return result;
+}
+
+// M x = rhs with the consistent Q1 mass matrix (hanging constraints included), by
+// Jacobi-preconditioned CG to a relative residual of 1e-14.  Used by the reverse mode
+// of mu^0 (M is symmetric, so its adjoint is the same solve).
+extern "C" chns_status chns_mass_solve(const chns_mesh* mc, const double* rhs, double* x, void* stream) {
+    chns_mesh* m = const_cast<chns_mesh*>(mc);
+    if (!m || !rhs || !x) { chns_set_error("null argument"); return CHNS_EINVAL; }
+    chns_status st = ensure_ws(m, m->ws ? m->ws->restart : 1);
+    if (st != CHNS_OK) return st;
+    SolverWS* ws = m->ws;
+    const int64_t N = m->dm.N;
+    const int D = m->dm.dim;
+    Ctx c{m, ws, (cudaStream_t)stream, N, grid_for(N)};
+    const int gE = (int)((m->dm.E + 127) / 128), gN = (int)((N + 255) / 256);
+    double* r = ws->dU;
+    double* z = ws->z64;
+    double* q = ws->t64;
+    double* dg = ws->V;
+    double* pvec = ws->V + N;
+    CHNS_CUDA(cudaMemsetAsync(dg, 0, N * sizeof(double), c.s));
+    { fill_kernel<<<c.g, 256, 0, c.s>>>(q, 1.0, N); chns_count_launches(1); }
+    if (D == 2) { mu_kernel<2, 1><<<gE, 128, 0, c.s>>>(m->dm, 0.0, nullptr, q, dg); chns_count_launches(1); }
+    else { mu_kernel<3, 1><<<gE, 128, 0, c.s>>>(m->dm, 0.0, nullptr, q, dg); chns_count_launches(1); }
+    CHNS_CUDA(cudaMemsetAsync(x, 0, N * sizeof(double), c.s));
+    { copy64_kernel<<<c.g, 256, 0, c.s>>>(rhs, r, N); chns_count_launches(1); }
+    { jacobi_kernel<<<gN, 256, 0, c.s>>>(dg, r, z, N); chns_count_launches(1); }
+    { copy64_kernel<<<c.g, 256, 0, c.s>>>(z, pvec, N); chns_count_launches(1); }
+    CHNS_CUDA(cudaGetLastError());
+    double rz, bb;
+    if ((st = dot_host(c, r, z, &rz)) != CHNS_OK) return st;
+    if ((st = dot_host(c, rhs, rhs, &bb)) != CHNS_OK) return st;
+    const double tol = 1e-14 * std::sqrt(bb);
+    int it = 0;
+    for (; it < 1000 && bb > 0.0; ++it) {
+        CHNS_CUDA(cudaMemsetAsync(q, 0, N * sizeof(double), c.s));
+        if (D == 2) { mu_kernel<2, 1><<<gE, 128, 0, c.s>>>(m->dm, 0.0, nullptr, pvec, q); chns_count_launches(1); }
+        else { mu_kernel<3, 1><<<gE, 128, 0, c.s>>>(m->dm, 0.0, nullptr, pvec, q); chns_count_launches(1); }
+        double pq, rr;
+        if ((st = dot_host(c, pvec, q, &pq)) != CHNS_OK) return st;
+        const double alpha = rz / pq;
+        { axpy_kernel<<<c.g, 256, 0, c.s>>>(alpha, pvec, x, N); chns_count_launches(1); }
+        { axpy_kernel<<<c.g, 256, 0, c.s>>>(-alpha, q, r, N); chns_count_launches(1); }
+        if ((st = dot_host(c, r, r, &rr)) != CHNS_OK) return st;
+        if (!std::isfinite(rr)) { chns_set_error("non-finite CG residual"); return CHNS_ENAN; }
+        if (std::sqrt(rr) <= tol) break;
+        { jacobi_kernel<<<gN, 256, 0, c.s>>>(dg, r, z, N); chns_count_launches(1); }
+        double rz2;
+        if ((st = dot_host(c, r, z, &rz2)) != CHNS_OK) return st;
+        { axpby_kernel<<<c.g, 256, 0, c.s>>>(1.0, z, rz2 / rz, pvec, N); chns_count_launches(1); }
+        rz = rz2;
+    }
     CHNS_CUDA(cudaGetLastError());
     CHNS_CUDA(cudaStreamSynchronize(c.s));
     if (it >= 1000) { chns_set_error("mass-matrix CG did not converge"); return CHNS_ENOCONV; }

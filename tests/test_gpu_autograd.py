@@ -1,0 +1,121 @@
+"""Differentiation through the hot path (torch.autograd.Function wrappers over the C-ABI):
+the residual's reverse and forward modes, the adjoint of an implicit step, and the
+gradient of the free energy after a checkpointed rollout with respect to the initial
+phi and Cn, checked against central finite differences; and J^T w against the oracle's
+assembled Jacobian on a level-3 3D mesh."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import Mesh as OMesh, Oracle, Params as OParams
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def chns():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_2009_06628_gb300 as chns
+    if not os.path.exists(chns.LIB_PATH):
+        from paper_2009_06628_gb300 import build
+        build.build()
+    chns.load()
+    return chns
+
+
+def small_problem(chns, dim=2, level=4, cfg_name="drop2d", seed=1, **over):
+    leaves = synth.uniform_leaves(dim, level)
+    gm = chns.Mesh(dim, level, leaves)
+    cfg = synth.config_params(cfg_name)
+    cfg.update(over)
+    x = gm.node_x()
+    U = np.zeros((gm.N, dim + 3))
+    U[:, dim + 1] = synth.drop_phi(x, [[0.5] * dim], [0.25], cfg["Cn"] * 2, noise=1e-2, seed=seed)
+    U[:, :dim] = synth.fourier_velocity(x, 4, seed + 1, 0.1)
+    bnd = np.any((x <= 0.0) | (x >= 1.0), axis=1)
+    U[bnd, :dim] = 0.0
+    return gm, chns.Params.make(**cfg), cfg, torch.tensor(U, device="cuda")
+
+
+def test_residual_function_modes(chns):
+    from paper_2009_06628_gb300.autograd import Residual
+    gm, prm, cfg, U = small_problem(chns)
+    U_old = U.clone()
+    chns.initial_mu(gm, prm, U_old)
+    rnd = lambda seed: torch.tensor(synth.random_vectors(U_old.numel(), 1, seed)[0], device="cuda").reshape(U_old.shape)
+    U_new = (U_old + 1e-3 * rnd(3)).contiguous()
+    w = rnd(4)
+    Cn = torch.tensor(cfg["Cn"], dtype=torch.float64, device="cuda", requires_grad=True)
+    Uo = U_old.clone().requires_grad_(True)
+    Un = U_new.clone().requires_grad_(True)
+    R = Residual.apply(gm, prm, Uo, Un, Cn)
+    (R * w).sum().backward()
+    gn, go, gc = chns.vjp(gm, prm, U_old, U_new, w)
+    assert torch.equal(Un.grad, gn) and torch.equal(Uo.grad, go)
+    assert float(Cn.grad) == float(gc[0])
+    # forward mode through torch.func matches the J x kernel
+    x = rnd(5)
+    Cn0 = torch.tensor(cfg["Cn"], dtype=torch.float64, device="cuda")
+    _, t = torch.func.jvp(lambda V: Residual.apply(gm, prm, U_old, V, Cn0), (U_new,), (x,))
+    assert torch.equal(t, chns.jvp(gm, prm, U_old, U_new, x))
+
+
+def test_rollout_gradient_matches_central_differences(chns):
+    from paper_2009_06628_gb300.autograd import rollout
+    gm, prm, cfg, U0 = small_problem(chns, dt=2e-3)
+    opts = chns.SolverOpts.make(rtol=1e-13, atol=1e-18, krylov_rtol=1e-10, precision=0, restart=120,
+                                max_krylov=20000, max_newton=30)
+    adj = chns.SolverOpts.make(krylov_rtol=1e-12, restart=120, max_krylov=20000, precision=0)
+    n_steps, every = 20, 5
+    d = gm.dim
+
+    def loss(phi0, cn, grad=False):
+        U = U0.clone()
+        U[:, d + 1] = phi0
+        return rollout(gm, prm, opts, adj, U, cn, n_steps, every)
+
+    phi0 = U0[:, d + 1].clone().requires_grad_(True)
+    Cn = torch.tensor(cfg["Cn"], dtype=torch.float64, device="cuda", requires_grad=True)
+    L = loss(phi0, Cn)
+    L.backward()
+    g_phi, g_cn = phi0.grad.clone(), float(Cn.grad)
+    eps = 1e-6
+    dirs = synth.random_vectors(gm.N, 8, 77)
+    with torch.no_grad():
+        for i in range(dirs.shape[0]):
+            v = torch.tensor(dirs[i], device="cuda")
+            lp = float(loss(phi0 + eps * v, Cn))
+            lm = float(loss(phi0 - eps * v, Cn))
+            fd = (lp - lm) / (2 * eps)
+            ad = float((g_phi * v).sum())
+            assert abs(fd - ad) <= 1e-5 * max(abs(fd), 1e-3), (i, fd, ad)
+        ec = 1e-6 * cfg["Cn"]
+        fd = (float(loss(phi0, Cn + ec)) - float(loss(phi0, Cn - ec))) / (2 * ec)
+        assert abs(fd - g_cn) <= 1e-5 * max(abs(fd), 1e-3), (fd, g_cn)
+
+
+def test_vjp_matches_assembled_oracle_jacobian_level3(chns):
+    leaves = synth.uniform_leaves(3, 3)
+    om = OMesh(3, 3, leaves)
+    gm = chns.Mesh(3, 3, leaves)
+    cfg = synth.config_params("drop3d")
+    o = Oracle(om)
+    oprm = OParams(**cfg)
+    prm = chns.Params.make(**cfg)
+    U = np.zeros((om.N, 6))
+    U[:, 4] = synth.drop_phi(om.x, [[0.5, 0.5, 0.5]], [0.3], 0.1, noise=1e-3, seed=9)
+    U[:, :3] = synth.fourier_velocity(om.x, 4, 10, 0.1)
+    U[om.boundary, :3] = 0.0
+    Ut = torch.tensor(U)
+    Un = Ut + 1e-3 * torch.tensor(synth.random_vectors(U.size, 1, 11)[0]).reshape(U.shape)
+    Un[torch.tensor(om.boundary), :3] = 0.0
+    J = o.jacobian(oprm, Ut, Un)
+    for seed in (12, 13):
+        w = torch.tensor(synth.random_vectors(U.size, 1, seed)[0]).reshape(U.shape)
+        gn, _, _ = chns.vjp(gm, prm, Ut.cuda(), Un.cuda(), w.cuda())
+        ref = (J.T @ w.reshape(-1)).reshape(U.shape)
+        assert float((gn.cpu() - ref).norm() / ref.norm()) <= 1e-12
