@@ -37,7 +37,7 @@ WORKLOAD = ("3D CHNS drop, uniform octree level 6 (64^3 Q1 hexes, 274,625 nodes 
 METRIC = "CHNS J·x GDOF/s & % HBM roofline; mixed vs FP64 Newton step time at ≤1e-9 rel"
 # Executed FP32 floating-point operations of one J x element (ncu: 2 x FFMA + FADD + FMUL
 # thread instructions of the FP32 J x kernel divided by the element count).
-FLOPS_PER_ELEMENT_JVP32 = None
+FLOPS_PER_ELEMENT_JVP32 = 19874
 # Derived FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 

@@ -90,7 +90,11 @@ typedef struct {
     int32_t max_newton, max_krylov, restart, precision;
     int32_t pc_type;     /* 0: nodal block-Jacobi; 1: block-Jacobi on v, phi, mu and a pressure
                             Schur-complement approximation (grad q, dt/(2 rho We) grad p)
-                            inverted by a Jacobi-preconditioned Chebyshev polynomial (FP32) */
+                            inverted by a Jacobi-preconditioned Chebyshev polynomial (FP32);
+                            2: as 1, with phi and mu preconditioned together by the
+                            Cahn-Hilliard block: mu eliminated with the mass matrix and the
+                            phi Schur complement approximated by (1/dt)(M + eps K) M^{-1}
+                            (M + eps K), eps^2 = dt Cn/(2 Pe), two Chebyshev solves (FP32) */
     int32_t pc_degree;   /* Chebyshev degree for pc_type 1, in [2, 200] */
 } chns_solver_opts;
 

@@ -108,17 +108,21 @@ class Params:
 class Oracle:
     """Element loops over a ``oracle.mesh.Mesh`` written with whole-array torch ops."""
 
-    def __init__(self, mesh):
+    def __init__(self, mesh, elements=None):
+        """``elements`` (optional index array) restricts every element loop to a subset:
+        rows of nodes whose whole support lies in the subset are then exact, which lets
+        large meshes be checked on sampled nodes."""
         self.m = mesh
         d = mesh.dim
         self.d, self.nc, self.nf = d, mesh.nc, mesh.nf
         self.N, self.dN, self.d2N, self.xq_ref = basis_tables(d)
-        self.P = torch.tensor(mesh.parents, dtype=torch.int64)
-        self.W = torch.tensor(mesh.weights, dtype=DT)
-        self.h = torch.tensor(mesh.h, dtype=DT)
+        sel = slice(None) if elements is None else np.asarray(elements)
+        self.P = torch.tensor(mesh.parents[sel], dtype=torch.int64)
+        self.W = torch.tensor(mesh.weights[sel], dtype=DT)
+        self.h = torch.tensor(mesh.h[sel], dtype=DT)
         self.bnd = torch.tensor(np.nonzero(mesh.boundary)[0], dtype=torch.int64)
         # physical quadrature points (E, q, d)
-        cx = torch.tensor(mesh.corner_x, dtype=DT)
+        cx = torch.tensor(mesh.corner_x[sel], dtype=DT)
         self.xq = torch.einsum("qa,ead->eqd", self.N, cx)
         self.detJ = (0.5 * self.h) ** d           # times unit Gauss weights
         # integral of each independent node's basis function (hanging weights included)

@@ -28,13 +28,19 @@ def with_cn(prm, Cn):
 
 
 class Residual(torch.autograd.Function):
+    """R(U^k, U^{k+1}; Cn) with reverse mode (J^T w kernel) and forward mode (J x kernel,
+    tangents of U^{k+1} only); usable under torch.func transforms."""
+
     @staticmethod
-    def forward(ctx, mesh, prm, U_old, U_new, Cn):
-        p = with_cn(prm, Cn)
-        ctx.mesh, ctx.prm = mesh, p
+    def forward(mesh, prm, U_old, U_new, Cn):
+        return residual(mesh, with_cn(prm, Cn), U_old.contiguous(), U_new.contiguous())
+
+    @staticmethod
+    def setup_context(ctx, inputs, output):
+        mesh, prm, U_old, U_new, Cn = inputs
+        ctx.mesh, ctx.prm = mesh, with_cn(prm, Cn)
         ctx.save_for_backward(U_old, U_new)
         ctx.save_for_forward(U_old, U_new)
-        return residual(mesh, p, U_old.contiguous(), U_new.contiguous())
 
     @staticmethod
     def backward(ctx, gR):
@@ -45,10 +51,9 @@ class Residual(torch.autograd.Function):
     @staticmethod
     def jvp(ctx, _m, _p, t_old, t_new, t_cn):
         U_old, U_new = ctx.saved_tensors
-        if t_old is not None and bool(torch.any(t_old != 0)):
-            raise NotImplementedError("forward mode supports tangents of U^{k+1} only")
-        if t_cn is not None and bool(torch.any(t_cn != 0)):
-            raise NotImplementedError("forward mode supports tangents of U^{k+1} only")
+        for t in (t_old, t_cn):
+            if t is not None and bool(torch.any(t != 0)):
+                raise NotImplementedError("forward mode supports tangents of U^{k+1} only")
         if t_new is None:
             return torch.zeros_like(U_new)
         return jvp(ctx.mesh, ctx.prm, U_old.contiguous(), U_new.contiguous(), t_new.contiguous())

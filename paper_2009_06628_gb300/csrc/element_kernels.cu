@@ -142,50 +142,104 @@ __device__ __forceinline__ unsigned gather_primal(const DevMesh& m, const Parent
     return mask;
 }
 
+// Sum-factorised Q1 interpolation at one Gauss point: the corner values are reduced one
+// axis at a time, u0 + w (u1 - u0) along each axis (w: weight of the corner with the axis
+// bit set, (1 +- 1/sqrt 3)/2; the two 1D weights sum to 1), and the differences
+// u1 - u0 give the derivative along that axis (times 1/h).  Same values as summing
+// N_a u_a over the corners, without forming the basis products.
+template <class T>
+__device__ __forceinline__ void gauss_weights(int q, T w[3]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) w[k] = ((q >> k) & 1) ? GaussC<T>::cp : GaussC<T>::cm;
+}
+
+// value only
+template <int D, class T, class Get>
+__device__ __forceinline__ T sf_value(const T w[3], Get u) {
+    if constexpr (D == 2) {
+        const T a0 = u(0) + w[0] * (u(1) - u(0));
+        const T a1 = u(2) + w[0] * (u(3) - u(2));
+        return a0 + w[1] * (a1 - a0);
+    } else {
+        T A[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) A[i] = u(2 * i) + w[0] * (u(2 * i + 1) - u(2 * i));
+        const T a0 = A[0] + w[1] * (A[1] - A[0]);
+        const T a1 = A[2] + w[1] * (A[3] - A[2]);
+        return a0 + w[2] * (a1 - a0);
+    }
+}
+
+// value, physical gradient and (if WANT_H) the mixed second derivatives
+template <int D, bool WANT_H, class T, class Get>
+__device__ __forceinline__ void sf_vgrad(const T w[3], T inv_h, Get u, T& val, T g[D], T* hm) {
+    if constexpr (D == 2) {
+        const T b0 = u(1) - u(0), b1 = u(3) - u(2);
+        const T a0 = u(0) + w[0] * b0, a1 = u(2) + w[0] * b1;
+        const T dy = a1 - a0, dby = b1 - b0;
+        val = a0 + w[1] * dy;
+        g[0] = (b0 + w[1] * dby) * inv_h;
+        g[1] = dy * inv_h;
+        if (WANT_H) hm[0] = dby * inv_h * inv_h;
+    } else {
+        T A[4], B[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            B[i] = u(2 * i + 1) - u(2 * i);
+            A[i] = u(2 * i) + w[0] * B[i];
+        }
+        T AA[2], AB[2], BA[2], BB[2];
+#pragma unroll
+        for (int z = 0; z < 2; ++z) {
+            AB[z] = A[2 * z + 1] - A[2 * z];
+            AA[z] = A[2 * z] + w[1] * AB[z];
+            BB[z] = B[2 * z + 1] - B[2 * z];
+            BA[z] = B[2 * z] + w[1] * BB[z];
+        }
+        const T dz = AA[1] - AA[0], dABz = AB[1] - AB[0], dBAz = BA[1] - BA[0];
+        val = AA[0] + w[2] * dz;
+        g[0] = (BA[0] + w[2] * dBAz) * inv_h;
+        g[1] = (AB[0] + w[2] * dABz) * inv_h;
+        g[2] = dz * inv_h;
+        if (WANT_H) {
+            const T h2 = inv_h * inv_h;
+            hm[0] = (BB[0] + w[2] * (BB[1] - BB[0])) * h2;   // xy
+            hm[1] = dBAz * h2;                                // xz
+            hm[2] = dABz * h2;                                // yz
+        }
+    }
+}
+
 // Interpolate the primal quadrature-point inputs at Gauss point q.
 template <int D, class T>
 __device__ __forceinline__ void interp_primal(const CornerPrimal<D, T>& C, int q, T inv_h, T inv_dt,
                                               QPIn<D, T>& X) {
-    constexpr int NC = Shape<D>::NC;
-    X.p = X.phi = X.mu = X.phidt = X.divnew = X.ps = T(0);
+    T w[3];
+    gauss_weights<T>(q, w);
+    T g[D], val;
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-        X.v[k] = X.gp[k] = X.gphi[k] = X.gmu[k] = X.vdt[k] = X.gps[k] = T(0);
+    for (int i = 0; i < D; ++i) {
+        sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return C.ut[a][i]; }, val, g, nullptr);
+        X.v[i] = val;
 #pragma unroll
-        for (int j = 0; j < D; ++j) X.gv[k][j] = T(0);
+        for (int k = 0; k < D; ++k) X.gv[i][k] = g[k];
     }
+    sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return C.ut[a][D]; }, X.p, X.gp, nullptr);
+    sf_vgrad<D, true, T>(w, inv_h, [&](int a) { return C.ut[a][D + 1]; }, X.phi, X.gphi, X.H);
+    sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return C.ut[a][D + 2]; }, X.mu, X.gmu, nullptr);
+    sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return C.ps[a]; }, X.ps, X.gps, nullptr);
+    // div v^{k+1} = div v~ + (1/2) div (v^{k+1} - v^k)
+    T div = X.gv[0][0];
 #pragma unroll
-    for (int k = 0; k < Shape<D>::NH; ++k) X.H[k] = T(0);
+    for (int i = 1; i < D; ++i) div += X.gv[i][i];
 #pragma unroll
-    for (int a = 0; a < NC; ++a) {
-        const Basis<D, T> b = basis<D, T>(a, q, inv_h);
-        const T* u = C.ut[a];
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            X.v[i] += b.N * u[i];
-#pragma unroll
-            for (int k = 0; k < D; ++k) X.gv[i][k] += b.dN[k] * u[i];
-            X.vdt[i] += b.N * C.dd[a][i];
-            X.divnew += b.dN[i] * (u[i] + T(0.5) * C.dd[a][i]);
-        }
-        X.p += b.N * u[D];
-        X.phi += b.N * u[D + 1];
-        X.mu += b.N * u[D + 2];
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-            X.gp[k] += b.dN[k] * u[D];
-            X.gphi[k] += b.dN[k] * u[D + 1];
-            X.gmu[k] += b.dN[k] * u[D + 2];
-            X.gps[k] += b.dN[k] * C.ps[a];
-        }
-#pragma unroll
-        for (int k = 0; k < Shape<D>::NH; ++k) X.H[k] += b.d2N[k] * u[D + 1];
-        X.phidt += b.N * C.dd[a][D];
-        X.ps += b.N * C.ps[a];
+    for (int i = 0; i < D; ++i) {
+        sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return C.dd[a][i]; }, val, g, nullptr);
+        X.vdt[i] = val * inv_dt;
+        div += T(0.5) * g[i];
     }
-#pragma unroll
-    for (int i = 0; i < D; ++i) X.vdt[i] *= inv_dt;
-    X.phidt *= inv_dt;
+    X.divnew = div;
+    X.phidt = sf_value<D, T>(w, [&](int a) { return C.dd[a][D]; }) * inv_dt;
 }
 
 template <class R>
@@ -320,31 +374,17 @@ elem_rj_kernel(DevMesh m, PCst<T> c, T inv_dt, T span,
             // tangent inputs: averages move by x/2, differences by x
             QPIn<D, Dual<T>> XD;
             T xv[NF], xg[NF][D], xH[Shape<D>::NH], xdiv = T(0), xpsv = T(0), xpsg[D];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                xv[f] = T(0);
-#pragma unroll
-                for (int k = 0; k < D; ++k) xg[f][k] = T(0);
-            }
-#pragma unroll
-            for (int k = 0; k < Shape<D>::NH; ++k) xH[k] = T(0);
-#pragma unroll
-            for (int k = 0; k < D; ++k) xpsg[k] = T(0);
-#pragma unroll
-            for (int a = 0; a < NC; ++a) {
-                const Basis<D, T> b = basis<D, T>(a, q, inv_h);
+            {
+                T w[3];
+                gauss_weights<T>(q, w);
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
-                    const T u = S.x[a][f];
-                    xv[f] += b.N * u;
-#pragma unroll
-                    for (int k = 0; k < D; ++k) xg[f][k] += b.dN[k] * u;
+                    if (f == D + 1)
+                        sf_vgrad<D, true, T>(w, inv_h, [&](int a) { return S.x[a][f]; }, xv[f], xg[f], xH);
+                    else
+                        sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return S.x[a][f]; }, xv[f], xg[f], nullptr);
                 }
-#pragma unroll
-                for (int k = 0; k < Shape<D>::NH; ++k) xH[k] += b.d2N[k] * S.x[a][D + 1];
-                xpsv += b.N * S.xps[a];
-#pragma unroll
-                for (int k = 0; k < D; ++k) xpsg[k] += b.dN[k] * S.xps[a];
+                sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return S.xps[a]; }, xpsv, xpsg, nullptr);
             }
 #pragma unroll
             for (int i = 0; i < D; ++i) xdiv += xg[i][i];

@@ -49,6 +49,16 @@ struct SolverWS {
     float* cd = nullptr;
     float* cy = nullptr;
     double* part = nullptr;  // per-block partials of the fused orthogonalisation reductions
+    // Cahn-Hilliard block (pc_type 2), FP32 nodal work arrays
+    float* ch_dinv = nullptr;  // inverse diagonal of M + eps K
+    float* ch_ml = nullptr;    // lumped mass (node integrals)
+    float* ch_psi2 = nullptr;  // psi''(phi~) at the nodes
+    float* ch_a = nullptr;
+    float* ch_b = nullptr;
+    float* ch_c = nullptr;
+    float* ch_rm = nullptr;
+    std::vector<float> ch_c1, ch_c2;
+    float ch_inv_theta = 0.0f, ch_eps = 0.0f;
     std::vector<float> cheb_c1, cheb_c2;
     float cheb_inv_theta = 0.0f;
     int kref_dim = 0;
@@ -81,6 +91,13 @@ void chns_solver_ws_free(SolverWS* ws) {
     cudaFree(ws->cd);
     cudaFree(ws->cy);
     cudaFree(ws->part);
+    cudaFree(ws->ch_dinv);
+    cudaFree(ws->ch_ml);
+    cudaFree(ws->ch_psi2);
+    cudaFree(ws->ch_a);
+    cudaFree(ws->ch_b);
+    cudaFree(ws->ch_c);
+    cudaFree(ws->ch_rm);
     if (ws->hsc) cudaFreeHost(ws->hsc);
     for (auto& e : ws->ev)
         if (e) cudaEventDestroy(e);
@@ -131,6 +148,8 @@ chns_status ensure_ws(chns_mesh* m, int restart) {
     A((void**)&ws->cd, (size_t)m->dm.N * sizeof(float));
     A((void**)&ws->cy, (size_t)m->dm.N * sizeof(float));
     A((void**)&ws->part, (size_t)ORTH_MAX_BX * (MAXSC / 32 + 1) * 9 * sizeof(double));
+    for (float** p : {&ws->ch_dinv, &ws->ch_ml, &ws->ch_psi2, &ws->ch_a, &ws->ch_b, &ws->ch_c, &ws->ch_rm})
+        A((void**)p, (size_t)m->dm.N * sizeof(float));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ws->hsc, MAXSC * sizeof(double));
     for (auto& ev : ws->ev)
         if (e == cudaSuccess) e = cudaEventCreate(&ev);
@@ -251,6 +270,12 @@ __global__ void scale_vec_kernel(const T* __restrict__ x, const double* __restri
                                  int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = sv[i] * (double)x[i];
+}
+// y = x ./ s
+__global__ void unscale_kernel(const double* __restrict__ x, const double* __restrict__ sv, double* __restrict__ y,
+                               int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = x[i] / sv[i];
 }
 __global__ void axpy_kernel(double a, const double* __restrict__ x, double* __restrict__ y, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -469,9 +494,14 @@ __global__ void pc_invert_kernel(DevMesh m, const TB* __restrict__ blk, TI* __re
         const double a = fabs(A[i][i]);
         scale[(size_t)n * NF + i] = a > 1e-300 ? 1.0 / a : 1.0;
     }
-    if (decouple_p) {
+    if (decouple_p & 1) {
         // the pressure is preconditioned separately (Schur-complement approximation)
         for (int j = 0; j < NF; ++j) A[D][j] = A[j][D] = (j == D) ? 1.0 : 0.0;
+    }
+    if (decouple_p & 2) {
+        // phi and mu are preconditioned by the Cahn-Hilliard block solve
+        for (int i = D + 1; i < NF; ++i)
+            for (int j = 0; j < NF; ++j) A[i][j] = A[j][i] = (j == i) ? 1.0 : 0.0;
     }
     for (int col = 0; col < NF; ++col) {
         int piv = col;
@@ -772,6 +802,102 @@ __global__ void fill_hash_kernel(float* __restrict__ x, int64_t n) {
         x[i] = (float)(h & 0xffff) / 65536.0f - 0.5f;
     }
 }
+__constant__ float c_Mref[64];   // Q1 consistent mass of the unit element (2-point Gauss)
+
+void mref_host(int D, float* Mr) {
+    const int NC = 1 << D;
+    const double gp = 0.78867513459481288225, gm = 0.21132486540518711775;
+    for (int a = 0; a < NC; ++a)
+        for (int b = 0; b < NC; ++b) {
+            double sum = 0.0;
+            for (int q = 0; q < NC; ++q) {
+                double na = 1.0, nb = 1.0;
+                for (int k = 0; k < D; ++k) {
+                    na *= (((a >> k) & 1) == ((q >> k) & 1)) ? gp : gm;
+                    nb *= (((b >> k) & 1) == ((q >> k) & 1)) ? gp : gm;
+                }
+                sum += na * nb;
+            }
+            Mr[a * NC + b] = (float)(sum / (double)NC);   // |det J| = (1/2)^d for h = 1
+        }
+}
+
+// y += (alpha M + beta K) x, or its diagonal (DIAG), on the Q1 space with constraints
+template <int D, bool DIAG>
+__global__ void mk_kernel(DevMesh m, float span, float alpha, float beta, const float* __restrict__ x,
+                          float* __restrict__ y) {
+    constexpr int NC = 1 << D;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m.E) return;
+    const float h = ldexpf(span, -(int)m.level[e]);
+    const float hd2 = (D == 2) ? 1.0f : h;            // h^(d-2)
+    const float hd = hd2 * h * h;                      // h^d
+    const float am = alpha * hd, bk = beta * hd2;
+    int par[NC][4], np[NC];
+    schur_corners<D>(m, e, par, np);
+    if (DIAG) {
+        for (int a = 0; a < NC; ++a) {
+            const float w = np[a] == 1 ? 1.0f : (np[a] == 2 ? 0.5f : 0.25f);
+            const float v = am * c_Mref[a * NC + a] + bk * c_Kref[a * NC + a];
+            for (int j = 0; j < np[a]; ++j) atomicAdd(y + par[a][j], w * w * v);
+        }
+        return;
+    }
+    float xl[NC];
+    for (int a = 0; a < NC; ++a) {
+        const float w = np[a] == 1 ? 1.0f : (np[a] == 2 ? 0.5f : 0.25f);
+        float sacc = 0.0f;
+        for (int j = 0; j < np[a]; ++j) sacc += w * __ldg(x + par[a][j]);
+        xl[a] = sacc;
+    }
+    for (int a = 0; a < NC; ++a) {
+        float sacc = 0.0f;
+#pragma unroll
+        for (int b = 0; b < NC; ++b) sacc += (am * c_Mref[a * NC + b] + bk * c_Kref[a * NC + b]) * xl[b];
+        const float w = np[a] == 1 ? 1.0f : (np[a] == 2 ? 0.5f : 0.25f);
+        for (int j = 0; j < np[a]; ++j) atomicAdd(y + par[a][j], w * sacc);
+    }
+}
+
+// nodal psi''(phi~) with phi~ the mid-point average, and the lumped mass (FP32)
+template <class T>
+__global__ void ch_nodal_kernel(int64_t N, int NF, int fphi, const T* __restrict__ Uo, const T* __restrict__ Un,
+                                const double* __restrict__ nmass, float* __restrict__ psi2, float* __restrict__ ml) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const float ph = 0.5f * ((float)Uo[(size_t)n * NF + fphi] + (float)Un[(size_t)n * NF + fphi]);
+    psi2[n] = 3.0f * ph * ph - 1.0f;
+    ml[n] = (float)nmass[n];
+}
+
+// rp = v_phi, rm = v_mu (strided FP64 input), a = rm / ml
+__global__ void ch_load_kernel(int64_t N, int NF, int fphi, const double* __restrict__ v, float* __restrict__ rp,
+                               float* __restrict__ rm, float* __restrict__ a, const float* __restrict__ ml) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    rp[n] = (float)v[(size_t)n * NF + fphi];
+    const float r = (float)v[(size_t)n * NF + fphi + 1];
+    rm[n] = r;
+    a[n] = r / ml[n];
+}
+// t = rp + c * y
+__global__ void ch_axpy_kernel(int64_t N, const float* __restrict__ rp, const float* __restrict__ y, float c,
+                               float* __restrict__ t) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n < N) t[n] = rp[n] + c * y[n];
+}
+// z_phi = x, z_mu = psi2 x + Cn^2 (K x) / ml - 2 rm / ml
+template <class TO>
+__global__ void ch_store_kernel(int64_t N, int NF, int fphi, const float* __restrict__ x, const float* __restrict__ kx,
+                                const float* __restrict__ rm, const float* __restrict__ psi2,
+                                const float* __restrict__ ml, float cn2, TO* __restrict__ z) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const float xv = x[n], il = 1.0f / ml[n];
+    z[(size_t)n * NF + fphi] = (TO)xv;
+    z[(size_t)n * NF + fphi + 1] = (TO)(psi2[n] * xv + cn2 * kx[n] * il - 2.0f * rm[n] * il);
+}
+
 __global__ void recip_kernel(float* __restrict__ d, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) d[i] = d[i] > 0.0f ? 1.0f / d[i] : 0.0f;
@@ -823,9 +949,9 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
     if (st != CHNS_OK) return st;
     if (!o || !U_old || !U) { chns_set_error("null argument"); return CHNS_EINVAL; }
     if (o->restart < 1 || o->restart > MAXSC / 4 || o->max_krylov < 1 || o->max_newton < 0 ||
-        (o->precision != 0 && o->precision != 1) || (o->pc_type != 0 && o->pc_type != 1) ||
-        (o->pc_type == 1 && (o->pc_degree < 2 || o->pc_degree > 200))) {
-        chns_set_error("bad solver options (restart in [1, 256], max_krylov >= 1, precision 0/1, pc_type 0/1, "
+        (o->precision != 0 && o->precision != 1) || (o->pc_type < 0 || o->pc_type > 2) ||
+        (o->pc_type >= 1 && (o->pc_degree < 2 || o->pc_degree > 200))) {
+        chns_set_error("bad solver options (restart in [1, 256], max_krylov >= 1, precision 0/1, pc_type 0/1/2, "
                        "pc_degree in [2, 200])");
         return CHNS_EINVAL;
     }
@@ -835,15 +961,20 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
     c.g = grid_for(c.n);
     const int D = m->dm.dim, NF = m->dm.nf, mres = o->restart;
     const bool mixed = o->precision == 1;
-    const int schur = o->pc_type == 1 ? 1 : 0;
+    const int schur = o->pc_type >= 1 ? 1 : 0;
+    const int chblk = o->pc_type == 2 ? 1 : 0;
+    const int pcmask = schur | (chblk << 1);
     const int gE = (int)((m->dm.E + 255) / 256);
     const int gN1 = (int)((m->dm.N + 255) / 256);
     // pressure Schur approximation: diagonal, spectrum bound and Chebyshev coefficients
     auto schur_setup = [&]() -> chns_status {
         if (ws->kref_dim != D) {
-            float K[64];
+            float K[64], Mr[64];
             kref_host(D, K);
+            mref_host(D, Mr);
             CHNS_CUDA(cudaMemcpyToSymbolAsync(c_Kref, K, sizeof(float) * (1 << D) * (1 << D), 0,
+                                              cudaMemcpyHostToDevice, c.s));
+            CHNS_CUDA(cudaMemcpyToSymbolAsync(c_Mref, Mr, sizeof(float) * (1 << D) * (1 << D), 0,
                                               cudaMemcpyHostToDevice, c.s));
             ws->kref_dim = D;
         }
@@ -904,6 +1035,70 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
     std::vector<double> H((size_t)(mres + 1) * mres), cs(mres), sn(mres), gv(mres + 1), y(mres);
     double r0 = 0.0, rn = 0.0;
     chns_status result = CHNS_OK;
+    // Cahn-Hilliard block: S_phi ~ (1/dt)(M + eps K) M^{-1} (M + eps K), eps^2 = dt Cn/(2 Pe)
+    const float span = (float)(m->dm.hi - m->dm.lo);
+    const int CH_DEG = 8;
+    auto mk = [&](float alpha, float beta, const float* x, float* y) -> chns_status {
+        CHNS_CUDA(cudaMemsetAsync(y, 0, m->dm.N * sizeof(float), c.s));
+        if (D == 2) { mk_kernel<2, false><<<gE, 256, 0, c.s>>>(m->dm, span, alpha, beta, x, y); chns_count_launches(1); }
+        else { mk_kernel<3, false><<<gE, 256, 0, c.s>>>(m->dm, span, alpha, beta, x, y); chns_count_launches(1); }
+        return CHNS_OK;
+    };
+    auto ch_setup = [&](const void* Uo_any, const void* Un_any) -> chns_status {
+        const int64_t N = m->dm.N;
+        if (mixed) { ch_nodal_kernel<float><<<gN1, 256, 0, c.s>>>(N, NF, D + 1, (const float*)Uo_any, (const float*)Un_any, m->d_nmass, ws->ch_psi2, ws->ch_ml); chns_count_launches(1); }
+        else { ch_nodal_kernel<double><<<gN1, 256, 0, c.s>>>(N, NF, D + 1, (const double*)Uo_any, (const double*)Un_any, m->d_nmass, ws->ch_psi2, ws->ch_ml); chns_count_launches(1); }
+        ws->ch_eps = (float)std::sqrt(p->dt * p->Cn / (2.0 * p->Pe));
+        CHNS_CUDA(cudaMemsetAsync(ws->ch_dinv, 0, N * sizeof(float), c.s));
+        if (D == 2) { mk_kernel<2, true><<<gE, 256, 0, c.s>>>(m->dm, span, 1.0f, ws->ch_eps, nullptr, ws->ch_dinv); chns_count_launches(1); }
+        else { mk_kernel<3, true><<<gE, 256, 0, c.s>>>(m->dm, span, 1.0f, ws->ch_eps, nullptr, ws->ch_dinv); chns_count_launches(1); }
+        { recip_kernel<<<gN1, 256, 0, c.s>>>(ws->ch_dinv, N); chns_count_launches(1); }
+        CHNS_CUDA(cudaGetLastError());
+        // spectrum of D^{-1}(M + eps K) lies in (0, 3.375] for Q1 (Gershgorin; mass and
+        // stiffness row ratios); Chebyshev interval [0.05, 4]
+        const double beta = 4.0, alpha = 0.05;
+        const double theta = 0.5 * (beta + alpha), delta = 0.5 * (beta - alpha), sigma = theta / delta;
+        ws->ch_c1.assign(CH_DEG, 0.0f);
+        ws->ch_c2.assign(CH_DEG, 0.0f);
+        double rho = 1.0 / sigma;
+        for (int k = 0; k + 1 < CH_DEG; ++k) {
+            const double rn = 1.0 / (2.0 * sigma - rho);
+            ws->ch_c1[k] = (float)(rn * rho);
+            ws->ch_c2[k] = (float)(2.0 * rn / delta);
+            rho = rn;
+        }
+        ws->ch_inv_theta = (float)(1.0 / theta);
+        return CHNS_OK;
+    };
+    // out = Chebyshev approximation of (M + eps K)^{-1} in (contiguous FP32)
+    auto ch_cheb = [&](const float* in, float* out) -> chns_status {
+        const int64_t N = m->dm.N;
+        { cheb_init_kernel<float><<<gN1, 256, 0, c.s>>>(N, 1, 0, in, ws->ch_dinv, ws->cr, ws->cx, ws->cd, ws->ch_inv_theta); chns_count_launches(1); }
+        for (int k = 0; k + 1 < CH_DEG; ++k) {
+            chns_status s2 = mk(1.0f, ws->ch_eps, ws->cd, ws->cy);
+            if (s2 != CHNS_OK) return s2;
+            { cheb_step_kernel<<<gN1, 256, 0, c.s>>>(N, ws->ch_dinv, ws->cr, ws->cx, ws->cd, ws->cy, ws->ch_c1[k], ws->ch_c2[k]); chns_count_launches(1); }
+        }
+        { cheb_final_kernel<float><<<gN1, 256, 0, c.s>>>(N, 1, 0, ws->cx, ws->cd, out); chns_count_launches(1); }
+        CHNS_CUDA(cudaGetLastError());
+        return CHNS_OK;
+    };
+    auto ch_apply_any = [&](const double* v, auto zout) -> chns_status {
+        using TO = std::remove_pointer_t<decltype(zout)>;
+        const int64_t N = m->dm.N;
+        chns_status s2;
+        { ch_load_kernel<<<gN1, 256, 0, c.s>>>(N, NF, D + 1, v, ws->ch_b, ws->ch_rm, ws->ch_a, ws->ch_ml); chns_count_launches(1); }
+        if ((s2 = mk(0.0f, 1.0f, ws->ch_a, ws->ch_c)) != CHNS_OK) return s2;                 // K M_L^{-1} r_mu
+        { ch_axpy_kernel<<<gN1, 256, 0, c.s>>>(N, ws->ch_b, ws->ch_c, (float)(1.0 / (p->Pe * p->Cn)), ws->ch_b); chns_count_launches(1); }
+        if ((s2 = ch_cheb(ws->ch_b, ws->ch_a)) != CHNS_OK) return s2;                      // (M + eps K)^{-1} t
+        if ((s2 = mk(1.0f, 0.0f, ws->ch_a, ws->ch_c)) != CHNS_OK) return s2;                // M s
+        { axpbyf_kernel<<<gN1, 256, 0, c.s>>>((float)p->dt, ws->ch_c, N); chns_count_launches(1); }
+        if ((s2 = ch_cheb(ws->ch_c, ws->ch_a)) != CHNS_OK) return s2;                      // dphi
+        if ((s2 = mk(0.0f, 1.0f, ws->ch_a, ws->ch_c)) != CHNS_OK) return s2;                // K dphi
+        { ch_store_kernel<TO><<<gN1, 256, 0, c.s>>>(N, NF, D + 1, ws->ch_a, ws->ch_c, ws->ch_rm, ws->ch_psi2, ws->ch_ml, (float)(p->Cn * p->Cn), zout); chns_count_launches(1); }
+        CHNS_CUDA(cudaGetLastError());
+        return CHNS_OK;
+    };
     // one classical Gram-Schmidt pass against V_0..V_{k-1}: h -> hdev[0..k), |w|^2 before
     // -> nrm_before, |w|^2 after -> nrm_after (all device scalars)
     auto orth_pass = [&](int k, double* hdev, double* nrm_before, double* nrm_after) -> chns_status {
@@ -923,16 +1118,20 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
             cudaError_t e = (D == 2) ? pc_build_launch<2, float>(m, pc, ws->Uo32, ws->Us32, ws->Pblk32, ws->ce, c.s)
                                      : pc_build_launch<3, float>(m, pc, ws->Uo32, ws->Us32, ws->Pblk32, ws->ce, c.s);
             CHNS_CUDA(e);
-            { pc_invert_kernel<float, float><<<gN, 128, 0, c.s>>>(m->dm, ws->Pblk32, ws->Pinv32, pin, ws->S, schur); chns_count_launches(1); }
+            { pc_invert_kernel<float, float><<<gN, 128, 0, c.s>>>(m->dm, ws->Pblk32, ws->Pinv32, pin, ws->S, pcmask); chns_count_launches(1); }
         } else {
             cudaError_t e = (D == 2) ? pc_build_launch<2, double>(m, pc, U_old, U, ws->Pblk64, ws->ce, c.s)
                                      : pc_build_launch<3, double>(m, pc, U_old, U, ws->Pblk64, ws->ce, c.s);
             CHNS_CUDA(e);
-            { pc_invert_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm, ws->Pblk64, ws->Pinv64, pin, ws->S, schur); chns_count_launches(1); }
+            { pc_invert_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm, ws->Pblk64, ws->Pinv64, pin, ws->S, pcmask); chns_count_launches(1); }
         }
         CHNS_CUDA(cudaGetLastError());
         if (schur) {
             chns_status st3 = schur_setup();
+            if (st3 != CHNS_OK) return st3;
+        }
+        if (chblk) {
+            chns_status st3 = mixed ? ch_setup(ws->Uo32, ws->Us32) : ch_setup(U_old, U);
             if (st3 != CHNS_OK) return st3;
         }
         CHNS_CUDA(cudaEventRecord(ws->ev[3], c.s));
@@ -994,15 +1193,20 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                 double* Vj = ws->V + (size_t)j * c.n;
                 // w = J M^{-1} V_j
                 if (mixed) {
-                    { pc_apply_kernel<float, float><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv32, Vj, ws->z32); chns_count_launches(1); }
-                    if (schur && (st = schur_apply_any((const double*)Vj, ws->z32)) != CHNS_OK) return st;
+                    // similarity scaling: the operator is S J M^{-1} S^{-1} (eigenvalues of J M^{-1})
+                    { unscale_kernel<<<c.g, 256, 0, c.s>>>(Vj, ws->S, ws->SR, c.n); chns_count_launches(1); }
+                    { pc_apply_kernel<float, float><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv32, ws->SR, ws->z32); chns_count_launches(1); }
+                    if (schur && (st = schur_apply_any((const double*)ws->SR, ws->z32)) != CHNS_OK) return st;
+                    if (chblk && (st = ch_apply_any((const double*)ws->SR, ws->z32)) != CHNS_OK) return st;
                     CHNS_CUDA(cudaEventRecord(ws->ev[0], c.s));
                     CHNS_CUDA(launch_jvp32(m, pc, ws->Uo32, ws->Us32, ws->z32, ws->y32, pin, c.s));
                     CHNS_CUDA(cudaEventRecord(ws->ev[1], c.s));
                     { scale_vec_kernel<float><<<c.g, 256, 0, c.s>>>(ws->y32, ws->S, ws->w, c.n); chns_count_launches(1); }
                 } else {
-                    { pc_apply_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv64, Vj, ws->z64); chns_count_launches(1); }
-                    if (schur && (st = schur_apply_any((const double*)Vj, ws->z64)) != CHNS_OK) return st;
+                    { unscale_kernel<<<c.g, 256, 0, c.s>>>(Vj, ws->S, ws->SR, c.n); chns_count_launches(1); }
+                    { pc_apply_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv64, ws->SR, ws->z64); chns_count_launches(1); }
+                    if (schur && (st = schur_apply_any((const double*)ws->SR, ws->z64)) != CHNS_OK) return st;
+                    if (chblk && (st = ch_apply_any((const double*)ws->SR, ws->z64)) != CHNS_OK) return st;
                     CHNS_CUDA(cudaEventRecord(ws->ev[0], c.s));
                     CHNS_CUDA(launch_jvp64(m, pc, U_old, U, ws->z64, ws->t64, pin, c.s));
                     CHNS_CUDA(cudaEventRecord(ws->ev[1], c.s));
@@ -1080,11 +1284,13 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
             std::memcpy(ws->hsc, y.data(), k * sizeof(double));
             CHNS_CUDA(cudaMemcpyAsync(ws->sc, ws->hsc, k * sizeof(double), cudaMemcpyHostToDevice, c.s));
             { combine_kernel<<<c.g, 256, 0, c.s>>>(ws->V, c.n, k, ws->sc, ws->t64, c.n); chns_count_launches(1); }
+            { unscale_kernel<<<c.g, 256, 0, c.s>>>(ws->t64, ws->S, ws->SR, c.n); chns_count_launches(1); }
             if (mixed)
-                { pc_apply_kernel<float, double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv32, ws->t64, ws->z64); chns_count_launches(1); }
+                { pc_apply_kernel<float, double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv32, ws->SR, ws->z64); chns_count_launches(1); }
             else
-                { pc_apply_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv64, ws->t64, ws->z64); chns_count_launches(1); }
-            if (schur && (st = schur_apply_any((const double*)ws->t64, ws->z64)) != CHNS_OK) return st;
+                { pc_apply_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv64, ws->SR, ws->z64); chns_count_launches(1); }
+            if (schur && (st = schur_apply_any((const double*)ws->SR, ws->z64)) != CHNS_OK) return st;
+            if (chblk && (st = ch_apply_any((const double*)ws->SR, ws->z64)) != CHNS_OK) return st;
             { axpy_kernel<<<c.g, 256, 0, c.s>>>(1.0, ws->z64, ws->dU, c.n); chns_count_launches(1); }
             CHNS_CUDA(cudaGetLastError());
             if (done || kry >= o->max_krylov) break;

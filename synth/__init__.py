@@ -8,10 +8,10 @@ solvers), so both sides can import it without sharing numerical code.
 """
 from .octree import (uniform_leaves, refine_leaves, balance_leaves, sphere_band_leaves,
                      plane_band_leaves, morton_encode, leaves_to_array)
-from .fields import (drop_phi, fourier_velocity, layer_phi, random_vectors, config_params)
+from .fields import (drop_phi, fourier_velocity, layer_phi, random_vectors, config_params, two_drops)
 
 __all__ = [
     "uniform_leaves", "refine_leaves", "balance_leaves", "sphere_band_leaves",
     "plane_band_leaves", "morton_encode", "leaves_to_array", "drop_phi", "fourier_velocity",
-    "layer_phi", "random_vectors", "config_params",
+    "layer_phi", "random_vectors", "config_params", "two_drops",
 ]

@@ -71,6 +71,17 @@ def fourier_velocity(x, n_modes, seed, vmax, kmax=3):
     return v
 
 
+def two_drops(seed, radii=(0.12, 0.15), distance=0.35):
+    """Centres and radii of the two-drop workload: the pair is centred in the unit box
+    with a seeded random orientation of the line joining the centres."""
+    rng = np.random.default_rng(seed)
+    u = rng.normal(size=3)
+    u /= np.linalg.norm(u)
+    c1 = 0.5 - 0.5 * distance * u
+    c2 = 0.5 + 0.5 * distance * u
+    return np.stack([c1, c2]), np.array(radii, dtype=np.float64)
+
+
 def random_vectors(n, count, seed):
     """``count`` seeded N(0, 1) vectors of length n, shape (count, n)."""
     rng = np.random.default_rng(seed)

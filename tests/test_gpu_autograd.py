@@ -55,21 +55,29 @@ def test_residual_function_modes(chns):
     R = Residual.apply(gm, prm, Uo, Un, Cn)
     (R * w).sum().backward()
     gn, go, gc = chns.vjp(gm, prm, U_old, U_new, w)
-    assert torch.equal(Un.grad, gn) and torch.equal(Uo.grad, go)
-    assert float(Cn.grad) == float(gc[0])
-    # forward mode through torch.func matches the J x kernel
+    # the kernels scatter with atomics, so two launches agree to rounding, not bitwise
+    assert torch.allclose(Un.grad, gn, rtol=1e-12, atol=1e-14 * float(gn.abs().max()))
+    assert torch.allclose(Uo.grad, go, rtol=1e-12, atol=1e-14 * float(go.abs().max()))
+    assert abs(float(Cn.grad) - float(gc[0])) <= 1e-12 * abs(float(gc[0]))
+    # forward-mode AD through the Function matches the J x kernel
+    import torch.autograd.forward_ad as fwAD
     x = rnd(5)
     Cn0 = torch.tensor(cfg["Cn"], dtype=torch.float64, device="cuda")
-    _, t = torch.func.jvp(lambda V: Residual.apply(gm, prm, U_old, V, Cn0), (U_new,), (x,))
-    assert torch.equal(t, chns.jvp(gm, prm, U_old, U_new, x))
+    with fwAD.dual_level():
+        R_dual = Residual.apply(gm, prm, U_old, fwAD.make_dual(U_new, x), Cn0)
+        t = fwAD.unpack_dual(R_dual).tangent
+    ref = chns.jvp(gm, prm, U_old, U_new, x)
+    assert torch.allclose(t, ref, rtol=1e-12, atol=1e-14 * float(ref.abs().max()))
 
 
 def test_rollout_gradient_matches_central_differences(chns):
     from paper_2009_06628_gb300.autograd import rollout
-    gm, prm, cfg, U0 = small_problem(chns, dt=2e-3)
-    opts = chns.SolverOpts.make(rtol=1e-13, atol=1e-18, krylov_rtol=1e-10, precision=0, restart=120,
-                                max_krylov=20000, max_newton=30)
-    adj = chns.SolverOpts.make(krylov_rtol=1e-12, restart=120, max_krylov=20000, precision=0)
+    # 9 x 9 nodes x 5 fields: GMRES(256) is nearly a direct solve, so each implicit step is
+    # converged to rounding and central differences see a smooth map
+    gm, prm, cfg, U0 = small_problem(chns, level=3, dt=2e-3)
+    opts = chns.SolverOpts.make(rtol=1e-12, atol=1e-18, krylov_rtol=1e-12, precision=0, restart=256,
+                                max_krylov=4000, max_newton=12)
+    adj = chns.SolverOpts.make(krylov_rtol=1e-12, restart=256, max_krylov=4000, precision=0)
     n_steps, every = 20, 5
     d = gm.dim
 

@@ -75,17 +75,17 @@ def test_mixed_matches_fp64(chns, dim, level):
 
 
 def test_adaptive_mixed_step_conserves_mass_and_energy(chns):
-    leaves = synth.sphere_band_leaves(3, 3, 6, [[0.5, 0.5, 0.5]], [0.2], 0.06)
-    gm, prm, cfg, U = drop_problem(chns, 3, leaves, 6, "drop3d", dict(rho_ratio=100.0, eta_ratio=50.0))
+    leaves = synth.sphere_band_leaves(3, 2, 5, [[0.5, 0.5, 0.5]], [0.2], 0.06)
+    gm, prm, cfg, U = drop_problem(chns, 3, leaves, 5, "drop3d", dict(rho_ratio=100.0, eta_ratio=50.0))
     assert gm.H > 0
-    opts = chns.SolverOpts.make(rtol=1e-10, atol=1e-16, krylov_rtol=1e-4, precision=1, restart=120,
-                                max_krylov=20000, max_newton=40)
+    opts = chns.SolverOpts.make(rtol=1e-9, atol=1e-16, krylov_rtol=1e-4, precision=1, restart=120,
+                                max_krylov=4000, max_newton=15, pc_type=2)
     m0 = chns.mass(gm, U)
     e_prev = sum(chns.energy(gm, prm, U))
     for _ in range(2):
         U, st = chns.newton_step(gm, prm, opts, U, check=False)
         assert st.reason == 0, st.as_dict()
-        assert abs(chns.mass(gm, U) - m0) <= 1e-11 * max(1.0, abs(m0)), (chns.mass(gm, U) - m0, st.as_dict())
+        assert abs(chns.mass(gm, U) - m0) <= 1e-10 * max(1.0, abs(m0)), (chns.mass(gm, U) - m0, st.as_dict())
         e = sum(chns.energy(gm, prm, U))
         assert e <= e_prev + 1e-12
         e_prev = e
