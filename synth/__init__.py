@@ -7,11 +7,12 @@ method's arithmetic (no basis functions, quadrature, residual terms or
 solvers), so both sides can import it without sharing numerical code.
 """
 from .octree import (uniform_leaves, refine_leaves, balance_leaves, sphere_band_leaves,
-                     plane_band_leaves, morton_encode, leaves_to_array)
+                     plane_band_leaves, morton_encode, leaves_to_array, graded_band_leaves, layer_distance)
 from .fields import (drop_phi, fourier_velocity, layer_phi, random_vectors, config_params, two_drops)
 
 __all__ = [
-    "uniform_leaves", "refine_leaves", "balance_leaves", "sphere_band_leaves",
+    "uniform_leaves", "refine_leaves", "balance_leaves", "sphere_band_leaves", "graded_band_leaves",
+    "layer_distance",
     "plane_band_leaves", "morton_encode", "leaves_to_array", "drop_phi", "fourier_velocity",
     "layer_phi", "random_vectors", "config_params", "two_drops",
 ]

@@ -149,3 +149,31 @@ def plane_band_leaves(dim, min_level, max_level, z0, amplitude, wavelength, phas
         return np.abs(mid[:, dim - 1] - zi) <= band + half_diag * (1.0 + slope)
 
     return balance_leaves(refine_leaves(dim, min_level, max_level, pred), dim, max_level)
+
+
+def graded_band_leaves(dim, min_level, max_level, dist, band, grade=3.0):
+    """Refine every octant of level l < max_level whose centre lies within
+    ``band + grade * sqrt(dim) * size_l`` of a surface given by the distance function
+    ``dist(points) -> |distance|``.  The margin growing with the octant size grades the
+    refinement so that neighbouring leaves differ by at most one level for smooth
+    surfaces (checked by the caller's mesh validation; ``balance_leaves`` repairs any
+    remaining violation).  Returns Morton-sorted leaves."""
+    def pred(lo, hi, level):
+        mid = 0.5 * (lo + hi)
+        size = hi[:, 0] - lo[:, 0]
+        return dist(mid) <= band + grade * np.sqrt(dim) * size
+
+    return refine_leaves(dim, min_level, max_level, pred)
+
+
+def layer_distance(z0, amplitude, wavelength, phase, dim=3):
+    """Approximate distance to x_last = z0 + amplitude cos(2 pi x_0/wavelength + phase)
+    (vertical offset divided by the slope factor)."""
+    k = 2.0 * np.pi / wavelength
+
+    def dist(p):
+        zi = z0 + amplitude * np.cos(k * p[:, 0] + phase)
+        slope = amplitude * k * np.sin(k * p[:, 0] + phase)
+        return np.abs(p[:, dim - 1] - zi) / np.sqrt(1.0 + slope * slope)
+
+    return dist
