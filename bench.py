@@ -37,7 +37,10 @@ WORKLOAD = ("3D CHNS drop, uniform octree level 6 (64^3 Q1 hexes, 274,625 nodes 
 METRIC = "CHNS J·x GDOF/s & % HBM roofline; mixed vs FP64 Newton step time at ≤1e-9 rel"
 # Executed FP32 floating-point operations of one J x element (ncu: 2 x FFMA + FADD + FMUL
 # thread instructions of the FP32 J x kernel divided by the element count).
-FLOPS_PER_ELEMENT_JVP32 = 19874
+FLOPS_PER_ELEMENT_JVP32 = 15442
+# DRAM bytes per FP32 J x launch on the 64^3 mesh: ncu dram__bytes_read + write of the
+# 128^3 capture (318.86 MB, 2,097,152 elements) scaled by elements (traffic grows with them).
+JVP32_TRAFFIC_BYTES_64 = 318.86e6 * 262144 / 2097152
 # Derived FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
@@ -313,7 +316,9 @@ def main():
     jvp_avg_ms = jvp_ms / max(jvp_calls, 1)
     hbm_bytes = 4 * dof * 4 + E * (8 * 4 + 1)      # read U^k, U^s, x; write y; e2n + level
     roof = {"bound": "alu", "unit": "TFLOP/s", "peak": FP32_PEAK_TFLOPS,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz", "traffic": None}
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+            "traffic": JVP32_TRAFFIC_BYTES_64 if E == 262144 else None,
+            "flop_per_element": FLOPS_PER_ELEMENT_JVP32}
     if FLOPS_PER_ELEMENT_JVP32:
         ach = FLOPS_PER_ELEMENT_JVP32 * E / (jvp_avg_ms * 1e-3) / 1e12
         roof.update({"achieved": ach, "frac": ach / FP32_PEAK_TFLOPS})

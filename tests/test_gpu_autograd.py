@@ -75,7 +75,7 @@ def test_rollout_gradient_matches_central_differences(chns):
     # 9 x 9 nodes x 5 fields: GMRES(256) is nearly a direct solve, so each implicit step is
     # converged to rounding and central differences see a smooth map
     gm, prm, cfg, U0 = small_problem(chns, level=3, dt=2e-3)
-    opts = chns.SolverOpts.make(rtol=1e-11, atol=1e-18, krylov_rtol=1e-12, precision=0, restart=256,
+    opts = chns.SolverOpts.make(rtol=1e-10, atol=1e-18, krylov_rtol=1e-12, precision=0, restart=256,
                                 max_krylov=4000, max_newton=20)
     adj = chns.SolverOpts.make(krylov_rtol=1e-12, restart=256, max_krylov=4000, precision=0)
     n_steps, every = 20, 5
@@ -91,7 +91,10 @@ def test_rollout_gradient_matches_central_differences(chns):
     L = loss(phi0, Cn)
     L.backward()
     g_phi, g_cn = phi0.grad.clone(), float(Cn.grad)
-    eps = 1e-6
+    # the implicit steps are converged to 1e-10 (row-equilibrated norm; the pressure rows
+    # set a rounding floor just below), so the central differences use eps = 1e-5, where
+    # solver noise (~1e-5 relative) and truncation (~eps^2) both stay below the bar
+    eps = 1e-5
     dirs = synth.random_vectors(gm.N, 8, 77)
     with torch.no_grad():
         for i in range(dirs.shape[0]):
@@ -100,9 +103,8 @@ def test_rollout_gradient_matches_central_differences(chns):
             lm = float(loss(phi0 - eps * v, Cn))
             fd = (lp - lm) / (2 * eps)
             ad = float((g_phi * v).sum())
-            # steps converged to 1e-11: central differences with eps = 1e-6 carry ~1e-5 noise
             assert abs(fd - ad) <= 1e-4 * max(abs(fd), 1e-3), (i, fd, ad)
-        ec = 1e-6 * cfg["Cn"]
+        ec = 1e-5 * cfg["Cn"]
         fd = (float(loss(phi0, Cn + ec)) - float(loss(phi0, Cn - ec))) / (2 * ec)
         assert abs(fd - g_cn) <= 1e-4 * max(abs(fd), 1e-3), (fd, g_cn)
 
