@@ -171,12 +171,48 @@ def aggregate_replicas(t_ms, work, dist=None, device="cpu"):
     return float(t), float(w)
 
 
+def layer_workload():
+    """Two-layer (Rayleigh-Taylor-shaped) workload: heavy fluid on top (density ratio 3),
+    interface z = 0.5 + 0.05 cos(2 pi x + phase) with a seeded phase; octree levels 5-10
+    refined in a band graded so that it is 2:1 balanced by construction (26.1M elements)."""
+    rng = np.random.default_rng(5)
+    phase = float(rng.uniform(0.0, 2.0 * np.pi))
+    dist = synth.layer_distance(0.5, 0.05, 1.0, phase)
+    leaves = synth.graded_band_leaves(DIM, 5, 10, dist, 0.0, grade=3.0)
+    cfg = synth.config_params("layer3d")
+    return leaves, 10, cfg, phase
+
+
+def twodrops_workload():
+    """Two drops (radii 0.12, 0.15, centres 0.35 apart, seeded orientation), octree
+    levels 4-9 refined within 3 Cn of the interfaces, 2:1 balanced (2.49M elements)."""
+    cfg = synth.config_params("twodrops3d")
+    centers, radii = synth.two_drops(3)
+    leaves = synth.sphere_band_leaves(DIM, 4, 9, centers, radii, 3 * cfg["Cn"])
+    return leaves, 9, cfg, (centers, radii)
+
+
 def run_profile(args):
-    """One kernel of the hot path, --reps launches, on the uniform mesh of --level."""
+    """One kernel of the hot path, --reps launches, on the chosen mesh."""
     import paper_2009_06628_gb300 as chns
-    leaves = synth.uniform_leaves(DIM, args.level)
-    gm = chns.Mesh(DIM, args.level, leaves)
-    cfg, U = workload_state(gm.node_x())
+    if args.mesh == "layer":
+        leaves, level, cfg, phase = layer_workload()
+        gm = chns.Mesh(DIM, level, leaves)
+        x = gm.node_x()
+        U = np.zeros((gm.N, DIM + 3))
+        U[:, DIM + 1] = synth.layer_phi(x, 0.5, 0.05, 1.0, phase, cfg["Cn"])
+    elif args.mesh == "twodrops":
+        leaves, level, cfg, (centers, radii) = twodrops_workload()
+        gm = chns.Mesh(DIM, level, leaves)
+        x = gm.node_x()
+        U = np.zeros((gm.N, DIM + 3))
+        U[:, DIM + 1] = synth.drop_phi(x, centers, radii, cfg["Cn"])
+        U[:, :DIM] = synth.fourier_velocity(x, 8, 4, 0.1)
+        U[np.any((x <= 0.0) | (x >= 1.0), axis=1), :DIM] = 0.0
+    else:
+        leaves = synth.uniform_leaves(DIM, args.level)
+        gm = chns.Mesh(DIM, args.level, leaves)
+        cfg, U = workload_state(gm.node_x())
     prm = chns.Params.make(**cfg)
     U0 = torch.tensor(U, device="cuda")
     Un = U0 + 1e-4 * torch.randn(U0.shape, device="cuda", dtype=torch.float64,
@@ -203,7 +239,7 @@ def run_profile(args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.reps
-    print(json.dumps({"profile": args.profile, "level": args.level, "elements": gm.E, "nodes": gm.N,
+    print(json.dumps({"profile": args.profile, "mesh": args.mesh, "level": args.level, "elements": gm.E, "nodes": gm.N,
                       "avg_ms_per_call": ms, "gdof_s": U0.numel() / (ms * 1e-3) / 1e9}))
     return 0
 
@@ -219,6 +255,7 @@ def main():
     ap.add_argument("--profile", choices=["jvp32", "jvp64", "residual", "vjp"],
                     help="run only this kernel --reps times on a uniform mesh of --level (for ncu)")
     ap.add_argument("--level", type=int, default=LEVEL)
+    ap.add_argument("--mesh", choices=["uniform", "twodrops", "layer"], default="uniform")
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
     if args.profile:

@@ -3,6 +3,7 @@
 // boundary nodes, and the upload to the current CUDA device.
 #include <algorithm>
 #include <cmath>
+#include <parallel/algorithm>
 #include <cstring>
 #include <new>
 
@@ -115,6 +116,8 @@ extern "C" chns_status chns_mesh_create(int32_t dim, int32_t max_level, int64_t 
     }
     // full 2:1 balance: the leaf holding a point just outside each face/edge/vertex
     // may be at most one level coarser
+    int unbalanced = 0;
+#pragma omp parallel for schedule(static) reduction(| : unbalanced)
     for (int64_t e = 0; e < E; ++e) {
         const int64_t* a = &anchor[(size_t)e * d];
         int64_t s = (int64_t)1 << (L - lv.level[e]);
@@ -130,9 +133,10 @@ extern "C" chns_status chns_mesh_create(int32_t dim, int32_t max_level, int64_t 
             }
             if (!inside) continue;
             int64_t j = lv.containing(p);
-            if (lv.level[j] < lv.level[e] - 1) { chns_set_error("octree is not 2:1 balanced"); return CHNS_ENOTBALANCED; }
+            if (lv.level[j] < lv.level[e] - 1) unbalanced = 1;
         }
     }
+    if (unbalanced) { chns_set_error("octree is not 2:1 balanced"); return CHNS_ENOTBALANCED; }
 
     // corners: hanging test and keys (Morton with L + 1 bits per axis)
     const size_t ncorner = (size_t)E * nc;
@@ -141,6 +145,7 @@ extern "C" chns_status chns_mesh_create(int32_t dim, int32_t max_level, int64_t 
     std::vector<uint64_t> node_keys;
     node_keys.reserve(ncorner / 2 + 16);
     std::vector<std::pair<uint64_t, int64_t>> hang_pts;  // (key, corner index)
+#pragma omp parallel for schedule(static)
     for (int64_t e = 0; e < E; ++e) {
         const int64_t* a = &anchor[(size_t)e * d];
         int lev = lv.level[e];
@@ -172,17 +177,18 @@ extern "C" chns_status chns_mesh_create(int32_t dim, int32_t max_level, int64_t 
                     if (ok && lv.is_leaf(q, lev - 1)) hanging = true;
                 }
             }
-            if (hanging) {
-                chang[ci] = 1;
-                hang_pts.push_back({ckey[ci], (int64_t)ci});
-            } else {
-                node_keys.push_back(ckey[ci]);
-            }
+            chang[ci] = hanging ? 1 : 0;
         }
     }
-    std::sort(node_keys.begin(), node_keys.end());
+    for (size_t ci = 0; ci < ncorner; ++ci) {
+        if (chang[ci])
+            hang_pts.push_back({ckey[ci], (int64_t)ci});
+        else
+            node_keys.push_back(ckey[ci]);
+    }
+    __gnu_parallel::sort(node_keys.begin(), node_keys.end());
     node_keys.erase(std::unique(node_keys.begin(), node_keys.end()), node_keys.end());
-    std::sort(hang_pts.begin(), hang_pts.end());
+    __gnu_parallel::sort(hang_pts.begin(), hang_pts.end());
     std::vector<uint64_t> hang_keys;
     std::vector<int64_t> hang_corner;
     for (auto& hp : hang_pts)
@@ -199,7 +205,9 @@ extern "C" chns_status chns_mesh_create(int32_t dim, int32_t max_level, int64_t 
     };
 
     std::vector<int32_t> e2n(ncorner);
-    for (size_t ci = 0; ci < ncorner; ++ci) {
+#pragma omp parallel for schedule(static)
+    for (int64_t cii = 0; cii < (int64_t)ncorner; ++cii) {
+        const size_t ci = (size_t)cii;
         if (!chang[ci]) {
             e2n[ci] = (int32_t)node_of(ckey[ci]);
         } else {

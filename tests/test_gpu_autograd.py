@@ -28,13 +28,16 @@ def chns():
 
 
 def small_problem(chns, dim=2, level=4, cfg_name="drop2d", seed=1, **over):
+    """A drop whose phase field stays within [-0.8, 0.8]: the pull-back clip of phi at
+    +-1 is a kink of the residual, where Newton and central differences both lose their
+    smoothness, so the derivative checks keep clear of it."""
     leaves = synth.uniform_leaves(dim, level)
     gm = chns.Mesh(dim, level, leaves)
     cfg = synth.config_params(cfg_name)
     cfg.update(over)
     x = gm.node_x()
     U = np.zeros((gm.N, dim + 3))
-    U[:, dim + 1] = synth.drop_phi(x, [[0.5] * dim], [0.25], cfg["Cn"] * 2, noise=1e-2, seed=seed)
+    U[:, dim + 1] = 0.8 * synth.drop_phi(x, [[0.5] * dim], [0.25], cfg["Cn"] * 2, noise=1e-2, seed=seed)
     U[:, :dim] = synth.fourier_velocity(x, 4, seed + 1, 0.1)
     bnd = np.any((x <= 0.0) | (x >= 1.0), axis=1)
     U[bnd, :dim] = 0.0
@@ -75,7 +78,7 @@ def test_rollout_gradient_matches_central_differences(chns):
     # 9 x 9 nodes x 5 fields: GMRES(256) is nearly a direct solve, so each implicit step is
     # converged to rounding and central differences see a smooth map
     gm, prm, cfg, U0 = small_problem(chns, level=3, dt=2e-3)
-    opts = chns.SolverOpts.make(rtol=1e-10, atol=1e-18, krylov_rtol=1e-12, precision=0, restart=256,
+    opts = chns.SolverOpts.make(rtol=1e-10, atol=1e-13, krylov_rtol=1e-12, precision=0, restart=256,
                                 max_krylov=4000, max_newton=20)
     adj = chns.SolverOpts.make(krylov_rtol=1e-12, restart=256, max_krylov=4000, precision=0)
     n_steps, every = 20, 5
