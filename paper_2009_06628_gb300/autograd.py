@@ -15,8 +15,8 @@ import ctypes
 import torch
 import torch.utils.checkpoint
 
-from . import (Params, free_energy_grad, initial_mu, jvp, mass_solve, mu_rhs_vjp, newton_step, residual,
-               step_adjoint, vjp)
+from . import (ChnsError, Params, free_energy_grad, initial_mu, jvp, mass_solve, mu_rhs_vjp, newton_step,
+               residual, step_adjoint, vjp)
 
 
 def with_cn(prm, Cn):
@@ -122,10 +122,17 @@ def rollout(mesh, prm, opts, adj_opts, U0, Cn, n_steps, checkpoint_every=5):
     recomputed from phi and Cn).  Every ``checkpoint_every`` steps form one segment whose
     states are recomputed during the backward pass instead of stored."""
     U = InitialMu.apply(mesh, prm, U0, Cn)
+    failed = []
 
     def segment(U_in, Cn_in, k):
+        # a solver failure is re-raised after checkpoint() returns: an exception thrown
+        # through the non-reentrant checkpoint leaves its saved-tensor hooks installed
         for _ in range(k):
-            U_in = ImplicitStep.apply(mesh, prm, opts, adj_opts, U_in, Cn_in)
+            try:
+                U_in = ImplicitStep.apply(mesh, prm, opts, adj_opts, U_in, Cn_in)
+            except ChnsError as e:
+                failed.append(e)
+                break
         return U_in
 
     done = 0
@@ -135,5 +142,7 @@ def rollout(mesh, prm, opts, adj_opts, U0, Cn, n_steps, checkpoint_every=5):
             U = torch.utils.checkpoint.checkpoint(segment, U, Cn, k, use_reentrant=False)
         else:
             U = segment(U, Cn, k)
+        if failed:
+            raise failed[0]
         done += k
     return FreeEnergy.apply(mesh, prm, U, Cn)

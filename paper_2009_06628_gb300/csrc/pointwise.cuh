@@ -39,9 +39,17 @@ template <class T> __device__ __forceinline__ Dual<T> operator/(T a, Dual<T> b) 
     return {q, -q * b.d / b.v};
 }
 
-// x^(-1/2) with its derivative -1/2 x^(-3/2)
-__device__ __forceinline__ double inv_sqrt(double x) { return 1.0 / sqrt(x); }
-__device__ __forceinline__ float inv_sqrt(float x) { return 1.0f / sqrtf(x); }
+// x^(-1/2) with its derivative -1/2 x^(-3/2) (CUDA's rsqrt: at most a few ulp off, far
+// below the FP64 (1e-12) and FP32 (1e-5) parity bars)
+__device__ __forceinline__ double inv_sqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float inv_sqrt(float x) { return rsqrtf(x); }
+// 1/x with its derivative -x^(-2)
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float recip(float x) { return 1.0f / x; }
+template <class T> __device__ __forceinline__ Dual<T> recip(Dual<T> x) {
+    T r = recip(x.v);
+    return {r, -r * r * x.d};
+}
 template <class T> __device__ __forceinline__ Dual<T> inv_sqrt(Dual<T> x) {
     T r = inv_sqrt(x.v);
     return {r, T(-0.5) * r * r * r * x.d};
@@ -122,12 +130,14 @@ __device__ __forceinline__ void pointwise(const QPIn<D, S>& X, const PCst<R>& c,
 #pragma unroll
     for (int k = 1; k < D; ++k) vg = vg + X.v[k] * X.gphi[k];
     const S Rphi = X.phidt + X.phi * Rc + vg;
-    const S er = eta / (rho * c.Re);
-    const S rad_m = c.four_over_dt2 + g * vv + (g / c.Pe) * (vJ / rho) + (c.C_I * R(D) * g * g) * (er * er);
+    const S irho = recip(rho);
+    const S er = c.inv_Re * (eta * irho);
+    const S rad_m = c.four_over_dt2 + g * vv + (g * c.inv_Pe) * (vJ * irho) + (c.C_I * R(D) * g * g) * (er * er);
     const S tm = inv_sqrt(rad_m);
-    const S tc = R(1) / ((R(D) * g) * tm);
+    // tau_c = 1/(tr G tau_m) = tau_m rad_m / (D g)
+    const S tc = (tm * rad_m) * (R(1) / (R(D) * g));
     const S tp = inv_sqrt(c.four_over_dt2 + g * vv + (c.C_phi * R(D) * g * g) * (c.inv_PeCn * c.inv_PeCn));
-    const S tm_rho = tm / rho;
+    const S tm_rho = tm * irho;
     // momentum rows
     S a[D];
 #pragma unroll
@@ -199,15 +209,17 @@ __device__ __forceinline__ void pointwise_adjoint(const QPIn<D, double>& X, cons
                 (i == D - 1 ? c.inv_Fr * rho : 0.0);
     }
     const double Rphi = X.phidt + X.phi * Rc + vg;
-    const double er = eta / (rho * c.Re);
+    const double irho = 1.0 / rho, irho2 = irho * irho;
+    const double er = c.inv_Re * eta * irho;
     const double GG = double(D) * g * g;
-    const double rad_m = c.four_over_dt2 + g * vv + (g / c.Pe) * (vJ / rho) + c.C_I * GG * er * er;
-    const double tm = 1.0 / sqrt(rad_m);
-    const double tc = 1.0 / ((double(D) * g) * tm);
+    const double rad_m = c.four_over_dt2 + g * vv + (g * c.inv_Pe) * (vJ * irho) + c.C_I * GG * er * er;
+    const double tm = rsqrt(rad_m);
+    const double tc = tm * rad_m * (1.0 / (double(D) * g));
     const double rad_p = c.four_over_dt2 + g * vv + c.C_phi * GG * c.inv_PeCn * c.inv_PeCn;
-    const double tp = 1.0 / sqrt(rad_p);
+    const double tp = rsqrt(rad_p);
+    const double tm_rho = tm * irho;
     double a[D];
-    for (int j = 0; j < D; ++j) a[j] = tm * X.v[j] - (tm * tm / rho) * Rm[j] + c.inv_Pe * (tm / rho) * J[j];
+    for (int j = 0; j < D; ++j) a[j] = tm * X.v[j] - (tm * tm_rho) * Rm[j] + c.inv_Pe * tm_rho * J[j];
 
     // ---- reverse sweep ----
     double rhob = 0, etab = 0, tmb = 0, tcb = 0, tpb = 0, Rcb = 0, Rphib = 0, vvb = 0, vJb = 0;
@@ -220,7 +232,8 @@ __device__ __forceinline__ void pointwise_adjoint(const QPIn<D, double>& X, cons
     for (int k = 0; k < (D == 2 ? 1 : 3); ++k) Xb.H[k] = 0.0;
     Xb.p = Xb.phi = Xb.mu = Xb.phidt = Xb.divnew = Xb.ps = 0.0;
     Cnb = 0.0;
-    const double dJc = -c.Jc / Cn, dinvPeCn = -c.inv_PeCn / Cn, dCnWe = c.inv_We, dCn2 = 2.0 * Cn;
+    const double iCn = 1.0 / Cn;
+    const double dJc = -c.Jc * iCn, dinvPeCn = -c.inv_PeCn * iCn, dCnWe = c.inv_We, dCn2 = 2.0 * Cn;
 
     // potential: f0 = phi^3 - phi - mu, f1_i = Cn^2 gphi_i
     Xb.mu -= Fb.f0[D + 2];
@@ -236,10 +249,10 @@ __device__ __forceinline__ void pointwise_adjoint(const QPIn<D, double>& X, cons
         Xb.v[i] += (tp * Rphi - X.phi) * fb;
         tpb += X.v[i] * Rphi * fb;
         Rphib += X.v[i] * tp * fb;
-        Xb.phi += (-X.v[i] + (tm / rho) * Rm[i]) * fb;
-        tmb += (X.phi / rho) * Rm[i] * fb;
-        rhob -= (tm * X.phi / (rho * rho)) * Rm[i] * fb;
-        Rmb[i] += (tm / rho) * X.phi * fb;
+        Xb.phi += (-X.v[i] + tm_rho * Rm[i]) * fb;
+        tmb += (X.phi * irho) * Rm[i] * fb;
+        rhob -= (tm * X.phi * irho2) * Rm[i] * fb;
+        Rmb[i] += tm_rho * X.phi * fb;
         Xb.gmu[i] += c.inv_PeCn * fb;
         Cnb += dinvPeCn * X.gmu[i] * fb;
     }
@@ -247,9 +260,9 @@ __device__ __forceinline__ void pointwise_adjoint(const QPIn<D, double>& X, cons
     Xb.divnew += Fb.f0[D];
     for (int i = 0; i < D; ++i) {
         const double fb = Fb.f1[D][i];
-        tmb += Rm[i] / rho * fb;
-        rhob -= tm * Rm[i] / (rho * rho) * fb;
-        Rmb[i] += (tm / rho) * fb;
+        tmb += Rm[i] * irho * fb;
+        rhob -= tm * Rm[i] * irho2 * fb;
+        Rmb[i] += tm_rho * fb;
     }
     // momentum gradient part: f1_ij = Rm_i a_j - Cn_We gphi_i gphi_j + d_ij inv_We (rho tc Rc - p)
     //                                 + inv_Re eta gv_ij
@@ -273,11 +286,11 @@ __device__ __forceinline__ void pointwise_adjoint(const QPIn<D, double>& X, cons
     Xb.p -= c.inv_We * trace;
     // a_j = tm v_j - (tm^2/rho) Rm_j + inv_Pe (tm/rho) J_j
     for (int j = 0; j < D; ++j) {
-        tmb += ab[j] * (X.v[j] - 2.0 * tm / rho * Rm[j] + c.inv_Pe * J[j] / rho);
+        tmb += ab[j] * (X.v[j] - 2.0 * tm_rho * Rm[j] + c.inv_Pe * J[j] * irho);
         Xb.v[j] += tm * ab[j];
-        rhob += ab[j] * (tm * tm * Rm[j] - c.inv_Pe * tm * J[j]) / (rho * rho);
-        Rmb[j] -= (tm * tm / rho) * ab[j];
-        Jb[j] += c.inv_Pe * (tm / rho) * ab[j];
+        rhob += ab[j] * (tm * tm * Rm[j] - c.inv_Pe * tm * J[j]) * irho2;
+        Rmb[j] -= (tm * tm_rho) * ab[j];
+        Jb[j] += c.inv_Pe * tm_rho * ab[j];
     }
     // momentum value part: f0_i = rho (vdt_i + conv_i) - tm sum_j Rm_j gv_ij + inv_Pe Jgv_i
     //                             + [i == D-1] inv_Fr rho
@@ -299,15 +312,15 @@ __device__ __forceinline__ void pointwise_adjoint(const QPIn<D, double>& X, cons
         vvb += g * radpb;
         Cnb += radpb * c.C_phi * GG * 2.0 * c.inv_PeCn * dinvPeCn;
     }
-    tmb -= tcb * tc / tm;
+    tmb -= tcb * tc * tm * rad_m;   // d(1/(D g tm))/dtm = -tc/tm, and 1/tm = tm rad_m
     {
         const double radmb = -0.5 * tm * tm * tm * tmb;
         vvb += g * radmb;
-        vJb += (g / c.Pe) / rho * radmb;
-        rhob -= (g / c.Pe) * vJ / (rho * rho) * radmb;
+        vJb += (g * c.inv_Pe) * irho * radmb;
+        rhob -= (g * c.inv_Pe) * vJ * irho2 * radmb;
         // C_I GG (eta/(rho Re))^2
-        etab += 2.0 * c.C_I * GG * er / (rho * c.Re) * radmb;
-        rhob -= 2.0 * c.C_I * GG * er * er / rho * radmb;
+        etab += 2.0 * c.C_I * GG * er * irho * c.inv_Re * radmb;
+        rhob -= 2.0 * c.C_I * GG * er * er * irho * radmb;
     }
     // Rphi = phidt + phi Rc + v . gphi
     Xb.phidt += Rphib;

@@ -1,8 +1,12 @@
 // Newton's method of Section 3.4, matrix-free: each Newton iteration solves
 // J dU = -R (Eq. newton_linear_system) with right-preconditioned restarted GMRES whose
 // operator is the J x element kernel (FP32 in mixed mode, FP64 otherwise) and whose
-// preconditioner is nodal block-Jacobi; orthogonalisation (classical Gram-Schmidt,
-// twice), dots, norms, the residual and the update stay FP64 on the device.  The
+// preconditioner is nodal block-Jacobi (plus the pressure Schur and Cahn-Hilliard
+// blocks); orthogonalisation (classical Gram-Schmidt with selective re-orthogonalisation),
+// dots, norms, the residual and the update stay FP64 on the device.  With the pressure
+// level set by its mean (pin mode 2) J is singular (constant pressure); GMRES runs on
+// J + u m_p^T / |Omega| instead, which is nonsingular and has the zero-mean solution of
+// J dU = -R.  The
 // Hessenberg least-squares problem is solved on the host (one scalar read-back per
 // Krylov iteration).  Also: the consistent initial chemical potential by CG.
 #include <cuda_runtime.h>
@@ -269,7 +273,7 @@ __global__ void combine_kernel(const double* __restrict__ V, int64_t ld, int k, 
 }
 // y = s .* x (FP32 or FP64 x)
 template <class T>
-__global__ void scale_vec_kernel(const T* __restrict__ x, const double* __restrict__ sv, double* __restrict__ y,
+__global__ void scale_vec_kernel(const T* x, const double* __restrict__ sv, double* y,
                                  int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = sv[i] * (double)x[i];
@@ -618,12 +622,23 @@ __global__ void insert_mu_kernel(const double* __restrict__ in, int NF, int f, i
     if (n < N) U[(size_t)n * NF + f] = in[n];
 }
 // sum_n m_n v[n*NF + f] into per-block partials
-__global__ void field_mass_kernel(const double* __restrict__ m, const double* __restrict__ v, int NF, int f,
+template <class T>
+__global__ void field_mass_kernel(const double* __restrict__ m, const T* __restrict__ v, int NF, int f,
                                   int64_t N, double* partials) {
     double acc[1] = {0.0};
     for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
-        acc[0] += m[n] * v[(size_t)n * NF + f];
+        acc[0] += m[n] * (double)v[(size_t)n * NF + f];
     block_reduce_store<1>(acc, partials);
+}
+// y = sv .* x + a * sc[0] on the rows of field f: the scaled operator of
+// J' = J + u m_p^T / |Omega| (pin mode 2), u = |diag J| on the pressure rows, so S u = 1
+// there.  The rank-one term moves the null mode of J (constant pressure) off zero.
+template <class T>
+__global__ void scale_vec_pmean_kernel(const T* x, const double* __restrict__ sv, double* y,
+                                       int64_t n, int NF, int f, const double* __restrict__ sc, double a) {
+    const double s = a * sc[0];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = sv[i] * (double)x[i] + ((int)(i % NF) == f ? s : 0.0);
 }
 // v[n*NF + f] -= sc[0] * inv_vol
 __global__ void field_shift_kernel(double* __restrict__ v, int NF, int f, int64_t N, const double* __restrict__ sc,
@@ -1142,6 +1157,13 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
         CHNS_CUDA(cudaEventRecord(ws->ev[3], c.s));
         return CHNS_OK;
     };
+    // m_p^T v / |Omega| term of the pin-mode-2 operator: sum_n m_n v_p[n] into sc[610]
+    const double inv_vol = 1.0 / m->volume;
+    const int nbm = c.g < 1024 ? c.g : 1024;
+    auto pmean = [&](const auto* v) {
+        { field_mass_kernel<<<nbm, 256, 0, c.s>>>(m->d_nmass, v, NF, D, m->dm.N, m->d_partials); chns_count_launches(1); }
+        { final_reduce_kernel<<<1, 256, 0, c.s>>>(m->d_partials, nbm, 1, ws->sc + 610); chns_count_launches(1); }
+    };
     bool pc_pending = false;
     for (int it = 0;; ++it) {
         CHNS_CUDA(launch_residual(m, pc, U_old, U, ws->R, pin, c.s));
@@ -1203,19 +1225,27 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                     { pc_apply_kernel<float, float><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv32, ws->SR, ws->z32); chns_count_launches(1); }
                     if (schur && (st = schur_apply_any((const double*)ws->SR, ws->z32)) != CHNS_OK) return st;
                     if (chblk && (st = ch_apply_any((const double*)ws->SR, ws->z32)) != CHNS_OK) return st;
+                    if (pin == 2) pmean(ws->z32);
                     CHNS_CUDA(cudaEventRecord(ws->ev[0], c.s));
                     CHNS_CUDA(launch_jvp32(m, pc, ws->Uo32, ws->Us32, ws->z32, ws->y32, pin, c.s));
                     CHNS_CUDA(cudaEventRecord(ws->ev[1], c.s));
-                    { scale_vec_kernel<float><<<c.g, 256, 0, c.s>>>(ws->y32, ws->S, ws->w, c.n); chns_count_launches(1); }
+                    if (pin == 2)
+                        { scale_vec_pmean_kernel<float><<<c.g, 256, 0, c.s>>>(ws->y32, ws->S, ws->w, c.n, NF, D, ws->sc + 610, inv_vol); chns_count_launches(1); }
+                    else
+                        { scale_vec_kernel<float><<<c.g, 256, 0, c.s>>>(ws->y32, ws->S, ws->w, c.n); chns_count_launches(1); }
                 } else {
                     { unscale_kernel<<<c.g, 256, 0, c.s>>>(Vj, ws->Sd, ws->SR, c.n); chns_count_launches(1); }
                     { pc_apply_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv64, ws->SR, ws->z64); chns_count_launches(1); }
                     if (schur && (st = schur_apply_any((const double*)ws->SR, ws->z64)) != CHNS_OK) return st;
                     if (chblk && (st = ch_apply_any((const double*)ws->SR, ws->z64)) != CHNS_OK) return st;
+                    if (pin == 2) pmean(ws->z64);
                     CHNS_CUDA(cudaEventRecord(ws->ev[0], c.s));
                     CHNS_CUDA(launch_jvp64(m, pc, U_old, U, ws->z64, ws->t64, pin, c.s));
                     CHNS_CUDA(cudaEventRecord(ws->ev[1], c.s));
-                    { scale_vec_kernel<double><<<c.g, 256, 0, c.s>>>(ws->t64, ws->S, ws->w, c.n); chns_count_launches(1); }
+                    if (pin == 2)
+                        { scale_vec_pmean_kernel<double><<<c.g, 256, 0, c.s>>>(ws->t64, ws->S, ws->w, c.n, NF, D, ws->sc + 610, inv_vol); chns_count_launches(1); }
+                    else
+                        { scale_vec_kernel<double><<<c.g, 256, 0, c.s>>>(ws->t64, ws->S, ws->w, c.n); chns_count_launches(1); }
                 }
                 S.jvp_calls++;
                 // classical Gram-Schmidt with selective re-orthogonalisation
@@ -1314,7 +1344,12 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
             }
             S.jvp_calls++;
             { axpby_kernel<<<c.g, 256, 0, c.s>>>(-1.0, ws->R, -1.0, ws->w, c.n); chns_count_launches(1); }
-            { scale_vec_kernel<double><<<c.g, 256, 0, c.s>>>(ws->w, ws->S, ws->w, c.n); chns_count_launches(1); }
+            if (pin == 2) {
+                pmean(ws->dU);
+                { scale_vec_pmean_kernel<double><<<c.g, 256, 0, c.s>>>(ws->w, ws->S, ws->w, c.n, NF, D, ws->sc + 610, -inv_vol); chns_count_launches(1); }
+            } else {
+                { scale_vec_kernel<double><<<c.g, 256, 0, c.s>>>(ws->w, ws->S, ws->w, c.n); chns_count_launches(1); }
+            }
             double rr;
             if ((st = dot_host(c, ws->w, ws->w, &rr)) != CHNS_OK) return st;
             rnorm = std::sqrt(rr);
@@ -1448,6 +1483,14 @@ __global__ void field_sum_kernel(const double* __restrict__ v, int NF, int f, in
         acc[0] += v[(size_t)n * NF + f];
     block_reduce_store<1>(acc, partials);
 }
+// sum_n wt[n*NF + f] v[n*NF + f] into per-block partials
+__global__ void field_wdot_kernel(const double* __restrict__ wt, const double* __restrict__ v, int NF, int f,
+                                  int64_t N, double* partials) {
+    double acc[1] = {0.0};
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
+        acc[0] += wt[(size_t)n * NF + f] * v[(size_t)n * NF + f];
+    block_reduce_store<1>(acc, partials);
+}
 // v[n*NF + f] += a * m[n] * sc[0]
 __global__ void field_axpy_mass_kernel(double* __restrict__ v, int NF, int f, int64_t N, const double* __restrict__ m,
                                        const double* __restrict__ sc, double a) {
@@ -1484,7 +1527,16 @@ extern "C" chns_status chns_step_adjoint(const chns_mesh* mc, const chns_params*
     cudaError_t ce = (D == 2) ? pc_build_launch<2, double>(m, pc, U_old, U_new, ws->Pblk64, ws->ce, c.s)
                               : pc_build_launch<3, double>(m, pc, U_old, U_new, ws->Pblk64, ws->ce, c.s);
     CHNS_CUDA(ce);
-    { pc_invert_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm, ws->Pblk64, ws->Pinv64, pin, ws->S, nullptr, 0); chns_count_launches(1); }
+    { pc_invert_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm, ws->Pblk64, ws->Pinv64, pin, ws->S, ws->Sd, 0); chns_count_launches(1); }
+    // pin mode 2: J' = J + u m_p^T / |Omega| with u = |diag J| on the pressure rows is
+    // nonsingular, and J'^T lambda = P^T g has the solution of J^T lambda = P^T g with
+    // u^T lambda = 0 (GMRES on the singular J^T drifts along its null vector)
+    const double inv_vol = 1.0 / m->volume;
+    auto add_pmean_T = [&](const double* v, double* y) {
+        { field_wdot_kernel<<<nbk, 256, 0, c.s>>>(ws->Sd, v, NF, D, m->dm.N, m->d_partials); chns_count_launches(1); }
+        { final_reduce_kernel<<<1, 256, 0, c.s>>>(m->d_partials, nbk, 1, ws->sc + 820); chns_count_launches(1); }
+        { field_axpy_mass_kernel<<<c.g, 256, 0, c.s>>>(y, NF, D, m->dm.N, m->d_nmass, ws->sc + 820, inv_vol); chns_count_launches(1); }
+    };
     // b = P^T g: remove sum(g_p) * m / |Omega| from the pressure part (pin mode 2)
     double* b = ws->R;
     { copy64_kernel<<<c.g, 256, 0, c.s>>>(g, b, c.n); chns_count_launches(1); }
@@ -1517,6 +1569,7 @@ extern "C" chns_status chns_step_adjoint(const chns_mesh* mc, const chns_params*
                 double* Vj = ws->V + (size_t)j * c.n;
                 { pc_apply_T_kernel<double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv64, Vj, ws->z64); chns_count_launches(1); }
                 CHNS_CUDA(launch_vjp(m, pc, U_old, U_new, ws->z64, ws->w, nullptr, nullptr, pin, c.s));
+                if (pin == 2) add_pmean_T(ws->z64, ws->w);
                 S.jvp_calls++;
                 CHNS_CUDA(launch_multidot(m, ws->V, c.n, j + 1, ws->w, c.n, ws->sc, c.s));
                 { gs_update_kernel<<<c.g, 256, 0, c.s>>>(ws->V, c.n, j + 1, ws->sc, ws->w, c.n); chns_count_launches(1); }
@@ -1570,6 +1623,7 @@ extern "C" chns_status chns_step_adjoint(const chns_mesh* mc, const chns_params*
             if (done || kry >= o->max_krylov) break;
             // restart: r = b - J^T lambda
             CHNS_CUDA(launch_vjp(m, pc, U_old, U_new, lambda, ws->w, nullptr, nullptr, pin, c.s));
+            if (pin == 2) add_pmean_T(lambda, ws->w);
             S.jvp_calls++;
             { axpby_kernel<<<c.g, 256, 0, c.s>>>(1.0, b, -1.0, ws->w, c.n); chns_count_launches(1); }
             double rr;

@@ -104,3 +104,52 @@ def test_mass_energy_and_invariants_at_full_size(big):
     hmax = 2.0 ** -4
     scale = prm.We * rho_c / prm.Fr * (0.5 * hmax) ** 3 / hmax
     assert float(RH.abs().max()) <= 1e-11 * scale
+
+
+@pytest.fixture(scope="module")
+def layer():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import bench
+    import paper_2009_06628_gb300 as chns
+    chns.load()
+    leaves, level, cfg, phase = bench.layer_workload()
+    gm = chns.Mesh(3, level, leaves)
+    x = gm.node_x()
+    U = np.zeros((gm.N, 6))
+    U[:, 4] = synth.layer_phi(x, 0.5, 0.05, 1.0, phase, cfg["Cn"])
+    U[:, :3] = synth.fourier_velocity(x, 8, 6, 0.05)
+    U[np.any((x <= 0.0) | (x >= 1.0), axis=1), :3] = 0.0
+    return dict(chns=chns, gm=gm, cfg=cfg, x=x, U=torch.tensor(U, device="cuda"))
+
+
+def test_layer_mesh_invariants_at_26M_elements(layer):
+    """The ~20M-element layer workload through the kernels alone: mass row-sum
+    (Proposition 1), hydrostatic zero, and FP32 J x against FP64 J x."""
+    chns, gm, cfg, x, U = layer["chns"], layer["gm"], layer["cfg"], layer["x"], layer["U"]
+    assert gm.E > 20_000_000 and gm.H > 0
+    prm = chns.Params.make(**cfg)
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    Un = U + 1e-4 * torch.randn(U.shape, dtype=torch.float64, device="cuda", generator=gen)
+    bnd = torch.tensor(np.any((x <= 0.0) | (x >= 1.0), axis=1), device="cuda")
+    Un[bnd, :3] = 0.0
+    R = chns.residual(gm, prm, U, Un)
+    lhs = float(R[:, 4].sum())
+    rhs = (chns.mass(gm, Un) - chns.mass(gm, U)) / prm.dt
+    assert abs(lhs - rhs) <= 1e-8 * max(1.0, abs(rhs))
+    xv = torch.randn(U.shape, dtype=torch.float64, device="cuda", generator=gen)
+    y64 = chns.jvp(gm, prm, U, Un, xv)
+    y32 = chns.jvp(gm, prm, U.float(), Un.float(), xv.float())
+    assert float((y32.double() - y64).norm() / y64.norm()) <= 1e-5
+    # hydrostatic state
+    oprm = OParams(**cfg)
+    c = -0.4
+    rho_c = oprm.alpha * c + oprm.beta
+    H = torch.zeros_like(U)
+    H[:, 3] = torch.tensor(-(prm.We * rho_c / prm.Fr) * x[:, 2] + 0.7, device="cuda")
+    H[:, 4] = c
+    H[:, 5] = c ** 3 - c
+    RH = chns.residual(gm, prm, H, H)
+    hmax = 2.0 ** -5
+    scale = prm.We * rho_c / prm.Fr * (0.5 * hmax) ** 3 / hmax
+    assert float(RH.abs().max()) <= 1e-11 * scale
