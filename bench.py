@@ -8,7 +8,7 @@ discrete potential equation.
 
 One step = one mixed-precision Newton step (FP64 residual, FP32 block-Jacobi build,
 GMRES with the FP32 J x kernel, FP64 classical Gram-Schmidt, FP64 update) from the
-same U^k, to a relative residual of 1e-9.  value = DOF x (J x applications) / step
+same U^k, to a relative residual of 1e-9 (GMRES(30)).  value = DOF x (J x applications) / step
 time, i.e. the J x throughput sustained by the whole Newton step.  The dominant
 kernel's roofline uses the CUDA-event time of the J x launches taken inside the step.
 """
@@ -37,10 +37,10 @@ WORKLOAD = ("3D CHNS drop, uniform octree level 6 (64^3 Q1 hexes, 274,625 nodes 
 METRIC = "CHNS J·x GDOF/s & % HBM roofline; mixed vs FP64 Newton step time at ≤1e-9 rel"
 # Executed FP32 floating-point operations of one J x element (ncu: 2 x FFMA + FADD + FMUL
 # thread instructions of the FP32 J x kernel divided by the element count).
-FLOPS_PER_ELEMENT_JVP32 = 15442
+FLOPS_PER_ELEMENT_JVP32 = 14770
 # DRAM bytes per FP32 J x launch on the 64^3 mesh: ncu dram__bytes_read + write of the
-# 128^3 capture (318.86 MB, 2,097,152 elements) scaled by elements (traffic grows with them).
-JVP32_TRAFFIC_BYTES_64 = 318.86e6 * 262144 / 2097152
+# 128^3 capture (318.57 MB, 2,097,152 elements) scaled by elements (traffic grows with them).
+JVP32_TRAFFIC_BYTES_64 = 318.57e6 * 262144 / 2097152
 # Derived FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
@@ -192,9 +192,8 @@ def twodrops_workload():
     return leaves, 9, cfg, (centers, radii)
 
 
-def run_profile(args):
-    """One kernel of the hot path, --reps launches, on the chosen mesh."""
-    import paper_2009_06628_gb300 as chns
+def workload_mesh(chns, args):
+    """(device mesh, parameters, host state) of the workload chosen by --mesh / --level."""
     if args.mesh == "layer":
         leaves, level, cfg, phase = layer_workload()
         gm = chns.Mesh(DIM, level, leaves)
@@ -213,6 +212,13 @@ def run_profile(args):
         leaves = synth.uniform_leaves(DIM, args.level)
         gm = chns.Mesh(DIM, args.level, leaves)
         cfg, U = workload_state(gm.node_x())
+    return gm, cfg, U
+
+
+def run_profile(args):
+    """One kernel of the hot path, --reps launches, on the chosen mesh."""
+    import paper_2009_06628_gb300 as chns
+    gm, cfg, U = workload_mesh(chns, args)
     prm = chns.Params.make(**cfg)
     U0 = torch.tensor(U, device="cuda")
     Un = U0 + 1e-4 * torch.randn(U0.shape, device="cuda", dtype=torch.float64,
@@ -244,6 +250,64 @@ def run_profile(args):
     return 0
 
 
+def run_trajectory(args):
+    """--newton-steps mixed Newton steps on the chosen mesh (rel. residual 1e-9 each), with
+    the phi integral and the energy parts after every step; the first --fp64-steps are
+    repeated in FP64 along their own trajectory, and the per-field relative L2 difference
+    mixed vs FP64 (velocity, p, phi, mu) is reported after each of them."""
+    import paper_2009_06628_gb300 as chns
+    gm, cfg, U = workload_mesh(chns, args)
+    prm = chns.Params.make(**cfg)
+    d = DIM
+    U0 = torch.tensor(U, device="cuda")
+    chns.initial_mu(gm, prm, U0)
+    dof = U0.numel()
+    kw = dict(rtol=1e-9, atol=1e-14, krylov_rtol=1e-3, restart=args.restart, max_krylov=args.max_krylov,
+              pc_type=args.pc_type, pc_degree=8)
+    o32 = chns.SolverOpts.make(precision=1, **kw)
+    o64 = chns.SolverOpts.make(precision=0, **kw)
+    fields = {"v": slice(0, d), "p": slice(d, d + 1), "phi": slice(d + 1, d + 2), "mu": slice(d + 2, d + 3)}
+    out = {"run": args.mesh, "elements": gm.E, "nodes": gm.N, "dof": dof, "hanging": gm.H,
+           "mass0": chns.mass(gm, U0), "energy0": chns.energy(gm, prm, U0), "steps": []}
+    Um, U64 = U0.clone(), U0.clone()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for k in range(args.newton_steps):
+        ev[0].record()
+        Um_new, st = chns.newton_step(gm, prm, o32, Um, check=False)
+        ev[1].record()
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1])
+        rec = {"step": k + 1, "mixed_ms": ms, "stats": st.as_dict(),
+               "gdof_s": dof * st.jvp_calls / (ms * 1e-3) / 1e9,
+               "jvp_gdof_s": dof * st.jvp_calls / (st.jvp_ms * 1e-3) / 1e9 if st.jvp_ms > 0 else None,
+               "mass": chns.mass(gm, Um_new), "energy": chns.energy(gm, prm, Um_new)}
+        rec["mass_drift"] = rec["mass"] - out["mass0"]
+        if st.reason != 0:
+            out["steps"].append(rec)
+            print(json.dumps(rec), flush=True)
+            break
+        if k < args.fp64_steps:
+            ev[2].record()
+            U64_new, s64 = chns.newton_step(gm, prm, o64, U64, check=False)
+            ev[3].record()
+            torch.cuda.synchronize()
+            rec["fp64_ms"] = ev[2].elapsed_time(ev[3])
+            rec["fp64_stats"] = s64.as_dict()
+            rec["rel_err_mixed_vs_fp64"] = {
+                f: float((Um_new[:, sl] - U64_new[:, sl]).norm() / U64_new[:, sl].norm().clamp_min(1e-300))
+                for f, sl in fields.items()}
+            rec["rel_err_mixed_vs_fp64"]["all"] = float((Um_new - U64_new).norm() / U64_new.norm())
+            U64 = U64_new
+        Um = Um_new
+        out["steps"].append(rec)
+        print(json.dumps(rec), flush=True)
+    E = [sum(out["energy0"])] + [sum(r["energy"]) for r in out["steps"]]
+    out["energy_non_increasing"] = all(b <= a for a, b in zip(E, E[1:]))
+    out["max_abs_mass_drift"] = max(abs(r["mass_drift"]) for r in out["steps"])
+    print(json.dumps({k: v for k, v in out.items() if k != "steps"}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -257,9 +321,18 @@ def main():
     ap.add_argument("--level", type=int, default=LEVEL)
     ap.add_argument("--mesh", choices=["uniform", "twodrops", "layer"], default="uniform")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--run", action="store_true",
+                    help="multi-step Newton run on --mesh (mixed, and FP64 for --fp64-steps) instead of the bench")
+    ap.add_argument("--newton-steps", type=int, default=5)
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--restart", type=int, default=30)
+    ap.add_argument("--max-krylov", type=int, default=5000)
+    ap.add_argument("--pc-type", type=int, default=1)
     args = ap.parse_args()
     if args.profile:
         return run_profile(args)
+    if args.run:
+        return run_trajectory(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -282,7 +355,7 @@ def main():
     U0 = torch.tensor(U, device=dev)
     chns.initial_mu(gm, prm, U0)
     dof = U0.numel()
-    opts = chns.SolverOpts.make(rtol=1e-9, atol=1e-14, krylov_rtol=1e-3, precision=1, restart=60, max_krylov=2000,
+    opts = chns.SolverOpts.make(rtol=1e-9, atol=1e-14, krylov_rtol=1e-3, precision=1, restart=30, max_krylov=2000,
                                 pc_type=1, pc_degree=8)
     U1 = torch.empty_like(U0)
     for _ in range(args.warmup):
@@ -336,7 +409,7 @@ def main():
     # ---- FP64 Newton step on the same problem, and the mixed step's error against it ----
     newton = {"mixed_ms": t_ms / args.steps, "mixed_stats": stats[-1]}
     if not args.no_fp64:
-        o64 = chns.SolverOpts.make(rtol=1e-9, atol=1e-14, krylov_rtol=1e-3, precision=0, restart=60, max_krylov=2000,
+        o64 = chns.SolverOpts.make(rtol=1e-9, atol=1e-14, krylov_rtol=1e-3, precision=0, restart=30, max_krylov=2000,
                                    pc_type=1, pc_degree=8)
         U64 = torch.empty_like(U0)
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -369,7 +442,7 @@ def main():
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "elements": E, "nodes": gm.N, "dof": dof,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "l2": "inputs larger than L2 (GMRES basis 61 x 13.2 MB FP64 per step)"},
+                       "l2": "inputs larger than L2 (GMRES basis 31 x 13.2 MB FP64, J x operands 26 MB, per step)"},
             "jvp_kernel": {"avg_ms": jvp_avg_ms, "launches": jvp_calls, "gdof_s": dof / (jvp_avg_ms * 1e-3) / 1e9},
             "roofline": roof, "hbm": hbm, "newton": newton, "clocks": clk, "gpu_launches": launches,
             "e2e": {"value": e2e_value, "unit": "GDOF/s", "h2d_bytes_per_step": dof * 8,

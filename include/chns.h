@@ -98,6 +98,8 @@ typedef struct {
     int32_t pc_degree;   /* Chebyshev degree for pc_type 1, in [2, 200] */
 } chns_solver_opts;
 
+#define CHNS_HIST 32
+
 /* Statistics of one Newton step (filled also on CHNS_ENOCONV / ENAN / EBREAKDOWN);
  * res0 / res_final are row-equilibrated norms ||S R||_2. */
 typedef struct {
@@ -105,6 +107,10 @@ typedef struct {
     double res0, res_final, du_norm;
     double jvp_ms;       /* device time of the J x launches (CUDA events on the stream) */
     double pc_ms;        /* device time of the preconditioner builds */
+    double apply_ms;     /* device time of the preconditioner applications inside GMRES */
+    double orth_ms;      /* device time of the Gram-Schmidt passes (dots, update, norms) */
+    double res_hist[CHNS_HIST];     /* ||S R|| at Newton iterates 0 .. min(newton_its, CHNS_HIST - 1) */
+    int32_t krylov_hist[CHNS_HIST]; /* GMRES iterations of linear solves 0 .. CHNS_HIST - 1 */
 } chns_stats;
 
 /* Build a mesh from a Morton-sorted, complete, 2:1 balanced leaf list (Section 4:

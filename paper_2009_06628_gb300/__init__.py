@@ -56,10 +56,15 @@ class SolverOpts(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("newton_its", ctypes.c_int32), ("krylov_its", ctypes.c_int32), ("jvp_calls", ctypes.c_int32),
                 ("reason", ctypes.c_int32), ("res0", ctypes.c_double), ("res_final", ctypes.c_double),
-                ("du_norm", ctypes.c_double), ("jvp_ms", ctypes.c_double), ("pc_ms", ctypes.c_double)]
+                ("du_norm", ctypes.c_double), ("jvp_ms", ctypes.c_double), ("pc_ms", ctypes.c_double),
+                ("apply_ms", ctypes.c_double), ("orth_ms", ctypes.c_double),
+                ("res_hist", ctypes.c_double * 32), ("krylov_hist", ctypes.c_int32 * 32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if not k.endswith("_hist")}
+        d["res_hist"] = list(self.res_hist[:min(self.newton_its + 1, 32)])
+        d["krylov_hist"] = list(self.krylov_hist[:min(self.newton_its, 32)])
+        return d
 
 
 _lib = None

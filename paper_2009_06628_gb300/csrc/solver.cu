@@ -45,7 +45,7 @@ struct SolverWS {
     double* Pinv64 = nullptr;
     double* sc = nullptr;    // device scalars
     double* hsc = nullptr;   // pinned host scalars
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // J x and preconditioner timing
+    cudaEvent_t ev[8] = {};   // J x, preconditioner build / apply and Gram-Schmidt timing
     // pressure Schur-complement approximation (FP32)
     float* ce = nullptr;     // E element coefficients
     float* kdinv = nullptr;  // N inverse diagonal
@@ -198,37 +198,66 @@ __global__ void gs_update_kernel(const double* __restrict__ V, int64_t ld, int k
     }
 }
 // Fused h = V^T w for all k basis vectors (blockIdx.y picks 8 of them) and, in chunk 0,
-// also w . w: partials[(chunk * gridDim.x + block) * 9 + j].
+// also w . w: partials[(chunk * gridDim.x + block) * 9 + j].  The 8 dot products of a
+// warp are reduced by recursive halving (each exchange level hands half of the
+// remaining values to the partner lane): 9 FP64 shuffle-adds per warp instead of 40,
+// which matters because every FP64 add runs on the narrow FP64 pipe.
 __global__ void orth_dots_kernel(const double* __restrict__ V, int64_t ld, int k, const double* __restrict__ w,
                                  int64_t n, double* __restrict__ partials) {
     const int chunk = blockIdx.y;
     const int j0 = chunk * 8;
     const int kk = min(8, k - j0);
-    double acc[9];
+    double acc[8];
+    double nrm = 0.0;
 #pragma unroll
-    for (int j = 0; j < 9; ++j) acc[j] = 0.0;
+    for (int j = 0; j < 8; ++j) acc[j] = 0.0;
     const double* Vc = V + (size_t)j0 * ld;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double wi = w[i];
 #pragma unroll
         for (int j = 0; j < 8; ++j)
             if (j < kk) acc[j] += Vc[(size_t)j * ld + i] * wi;
-        if (chunk == 0) acc[8] += wi * wi;
+        if (chunk == 0) nrm += wi * wi;
     }
-    // block reduction of 9 values
-    __shared__ double sred[32][9];
+    const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // 8 -> 4 values (lane bit 4 keeps the upper half), 4 -> 2 (bit 3), 2 -> 1 (bit 2)
+    double t4[4], t2[2];
+    {
+        const bool up = lane & 16;
 #pragma unroll
-    for (int j = 0; j < 9; ++j) {
-        double v = acc[j];
+        for (int t = 0; t < 4; ++t) {
+            const double keep = up ? acc[4 + t] : acc[t];
+            const double give = up ? acc[t] : acc[4 + t];
+            t4[t] = keep + __shfl_xor_sync(full, give, 16);
+        }
+    }
+    {
+        const bool up = lane & 8;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (lane == 0) sred[warp][j] = v;
+        for (int t = 0; t < 2; ++t) {
+            const double keep = up ? t4[2 + t] : t4[t];
+            const double give = up ? t4[t] : t4[2 + t];
+            t2[t] = keep + __shfl_xor_sync(full, give, 8);
+        }
+    }
+    const bool up4 = lane & 4;
+    double t1 = (up4 ? t2[1] : t2[0]) + __shfl_xor_sync(full, up4 ? t2[0] : t2[1], 4);
+    t1 += __shfl_xor_sync(full, t1, 2);
+    t1 += __shfl_xor_sync(full, t1, 1);
+    // lane holds the warp sum of value ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)
+    __shared__ double sred[32][9];
+    if ((lane & 3) == 0) sred[warp][((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)] = t1;
+    if (chunk == 0) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) nrm += __shfl_xor_sync(full, nrm, off);
+        if (lane == 0) sred[warp][8] = nrm;
     }
     __syncthreads();
     if (threadIdx.x < 9) {
         double v = 0.0;
-        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) v += sred[w2][threadIdx.x];
+        if (threadIdx.x < 8 || chunk == 0)
+            for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) v += sred[w2][threadIdx.x];
         partials[((size_t)chunk * gridDim.x + blockIdx.x) * 9 + threadIdx.x] = v;
     }
 }
@@ -637,8 +666,12 @@ template <class T>
 __global__ void scale_vec_pmean_kernel(const T* x, const double* __restrict__ sv, double* y,
                                        int64_t n, int NF, int f, const double* __restrict__ sc, double a) {
     const double s = a * sc[0];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = sv[i] * (double)x[i] + ((int)(i % NF) == f ? s : 0.0);
+    const int64_t N = n / NF;
+    for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < N;
+         node += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i0 = node * NF;
+        for (int g = 0; g < NF; ++g) y[i0 + g] = sv[i0 + g] * (double)x[i0 + g] + (g == f ? s : 0.0);
+    }
 }
 // v[n*NF + f] -= sc[0] * inv_vol
 __global__ void field_shift_kernel(double* __restrict__ v, int NF, int f, int64_t N, const double* __restrict__ sc,
@@ -923,25 +956,28 @@ __global__ void recip_kernel(float* __restrict__ d, int64_t n) {
     if (i < n) d[i] = d[i] > 0.0f ? 1.0f / d[i] : 0.0f;
 }
 
-// r = v_p (strided input), x = 0, d = dinv r / theta
+// r = v_p (strided input), x = 0, d = dinv r / theta, y = 0 (the first matvec's output)
 template <class TI>
 __global__ void cheb_init_kernel(int64_t N, int NF, int f, const TI* __restrict__ v, const float* __restrict__ dinv,
-                                 float* __restrict__ r, float* __restrict__ x, float* __restrict__ d, float inv_theta) {
+                                 float* __restrict__ r, float* __restrict__ x, float* __restrict__ d, float* __restrict__ y,
+                                 float inv_theta) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     const float rv = (float)v[(size_t)n * NF + f];
     r[n] = rv;
     x[n] = 0.0f;
+    y[n] = 0.0f;
     d[n] = inv_theta * dinv[n] * rv;
 }
 
-// x += d; r -= y; d = c1 d + c2 dinv r
+// x += d; r -= y; d = c1 d + c2 dinv r; y = 0 (ready for the next accumulating matvec)
 __global__ void cheb_step_kernel(int64_t N, const float* __restrict__ dinv, float* __restrict__ r, float* __restrict__ x,
-                                 float* __restrict__ d, const float* __restrict__ y, float c1, float c2) {
+                                 float* __restrict__ d, float* __restrict__ y, float c1, float c2) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     x[n] += d[n];
     const float rn = r[n] - y[n];
+    y[n] = 0.0f;
     r[n] = rn;
     d[n] = c1 * d[n] + c2 * dinv[n] * rn;
 }
@@ -1030,9 +1066,8 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
         using TI = std::remove_const_t<std::remove_pointer_t<decltype(vin)>>;
         using TO = std::remove_pointer_t<decltype(zout)>;
         const int64_t N = m->dm.N;
-        { cheb_init_kernel<TI><<<gN1, 256, 0, c.s>>>(N, NF, D, vin, ws->kdinv, ws->cr, ws->cx, ws->cd, ws->cheb_inv_theta); chns_count_launches(1); }
+        { cheb_init_kernel<TI><<<gN1, 256, 0, c.s>>>(N, NF, D, vin, ws->kdinv, ws->cr, ws->cx, ws->cd, ws->cy, ws->cheb_inv_theta); chns_count_launches(1); }
         for (int k = 0; k + 1 < o->pc_degree; ++k) {
-            CHNS_CUDA(cudaMemsetAsync(ws->cy, 0, N * sizeof(float), c.s));
             if (D == 2) { schur_matvec_kernel<2><<<gE, 256, 0, c.s>>>(m->dm, ws->ce, ws->cd, ws->cy); chns_count_launches(1); }
             else { schur_matvec_kernel<3><<<gE, 256, 0, c.s>>>(m->dm, ws->ce, ws->cd, ws->cy); chns_count_launches(1); }
             { cheb_step_kernel<<<gN1, 256, 0, c.s>>>(N, ws->kdinv, ws->cr, ws->cx, ws->cd, ws->cy, ws->cheb_c1[k], ws->cheb_c2[k]); chns_count_launches(1); }
@@ -1093,7 +1128,7 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
     // out = Chebyshev approximation of (M + eps K)^{-1} in (contiguous FP32)
     auto ch_cheb = [&](const float* in, float* out) -> chns_status {
         const int64_t N = m->dm.N;
-        { cheb_init_kernel<float><<<gN1, 256, 0, c.s>>>(N, 1, 0, in, ws->ch_dinv, ws->cr, ws->cx, ws->cd, ws->ch_inv_theta); chns_count_launches(1); }
+        { cheb_init_kernel<float><<<gN1, 256, 0, c.s>>>(N, 1, 0, in, ws->ch_dinv, ws->cr, ws->cx, ws->cd, ws->cy, ws->ch_inv_theta); chns_count_launches(1); }
         for (int k = 0; k + 1 < CH_DEG; ++k) {
             chns_status s2 = mk(1.0f, ws->ch_eps, ws->cd, ws->cy);
             if (s2 != CHNS_OK) return s2;
@@ -1182,6 +1217,7 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
         rn = std::sqrt(rn);
         if (it == 0) r0 = rn;
         S.newton_its = it;
+        if (it < CHNS_HIST) S.res_hist[it] = rn;
         S.res0 = r0;
         S.res_final = rn;
         if (flag & 1u) { chns_set_error("a tau_m radicand was not positive"); result = CHNS_ETAU; break; }
@@ -1221,11 +1257,13 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                 // w = J M^{-1} V_j
                 if (mixed) {
                     // similarity scaling: the operator is S J M^{-1} S^{-1} (eigenvalues of J M^{-1})
+                    CHNS_CUDA(cudaEventRecord(ws->ev[4], c.s));
                     { unscale_kernel<<<c.g, 256, 0, c.s>>>(Vj, ws->Sd, ws->SR, c.n); chns_count_launches(1); }
                     { pc_apply_kernel<float, float><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv32, ws->SR, ws->z32); chns_count_launches(1); }
                     if (schur && (st = schur_apply_any((const double*)ws->SR, ws->z32)) != CHNS_OK) return st;
                     if (chblk && (st = ch_apply_any((const double*)ws->SR, ws->z32)) != CHNS_OK) return st;
                     if (pin == 2) pmean(ws->z32);
+                    CHNS_CUDA(cudaEventRecord(ws->ev[5], c.s));
                     CHNS_CUDA(cudaEventRecord(ws->ev[0], c.s));
                     CHNS_CUDA(launch_jvp32(m, pc, ws->Uo32, ws->Us32, ws->z32, ws->y32, pin, c.s));
                     CHNS_CUDA(cudaEventRecord(ws->ev[1], c.s));
@@ -1234,11 +1272,13 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                     else
                         { scale_vec_kernel<float><<<c.g, 256, 0, c.s>>>(ws->y32, ws->S, ws->w, c.n); chns_count_launches(1); }
                 } else {
+                    CHNS_CUDA(cudaEventRecord(ws->ev[4], c.s));
                     { unscale_kernel<<<c.g, 256, 0, c.s>>>(Vj, ws->Sd, ws->SR, c.n); chns_count_launches(1); }
                     { pc_apply_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv64, ws->SR, ws->z64); chns_count_launches(1); }
                     if (schur && (st = schur_apply_any((const double*)ws->SR, ws->z64)) != CHNS_OK) return st;
                     if (chblk && (st = ch_apply_any((const double*)ws->SR, ws->z64)) != CHNS_OK) return st;
                     if (pin == 2) pmean(ws->z64);
+                    CHNS_CUDA(cudaEventRecord(ws->ev[5], c.s));
                     CHNS_CUDA(cudaEventRecord(ws->ev[0], c.s));
                     CHNS_CUDA(launch_jvp64(m, pc, U_old, U, ws->z64, ws->t64, pin, c.s));
                     CHNS_CUDA(cudaEventRecord(ws->ev[1], c.s));
@@ -1252,8 +1292,10 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                 double hs[2 * 256 + 1];
                 for (int i = 0; i <= j; ++i) hs[256 + i] = 0.0;
                 {
+                    CHNS_CUDA(cudaEventRecord(ws->ev[6], c.s));
                     chns_status so = orth_pass(j + 1, ws->sc, ws->sc + 600, ws->sc + 601);
                     if (so != CHNS_OK) return so;
+                    CHNS_CUDA(cudaEventRecord(ws->ev[7], c.s));
                     CHNS_CUDA(cudaMemcpyAsync(ws->hsc, ws->sc, 602 * sizeof(double), cudaMemcpyDeviceToHost, c.s));
                     CHNS_CUDA(cudaStreamSynchronize(c.s));
                     for (int i = 0; i <= j; ++i) hs[i] = ws->hsc[i];
@@ -1263,6 +1305,7 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                     if (wn2 < 0.01 * w2) {
                         so = orth_pass(j + 1, ws->sc + 256, ws->sc + 602, ws->sc + 603);
                         if (so != CHNS_OK) return so;
+                        CHNS_CUDA(cudaEventRecord(ws->ev[7], c.s));
                         CHNS_CUDA(cudaMemcpyAsync(ws->hsc + 256, ws->sc + 256, 348 * sizeof(double),
                                                   cudaMemcpyDeviceToHost, c.s));
                         CHNS_CUDA(cudaStreamSynchronize(c.s));
@@ -1275,6 +1318,10 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                     float ms = 0.0f;
                     CHNS_CUDA(cudaEventElapsedTime(&ms, ws->ev[0], ws->ev[1]));
                     S.jvp_ms += ms;
+                    CHNS_CUDA(cudaEventElapsedTime(&ms, ws->ev[4], ws->ev[5]));
+                    S.apply_ms += ms;
+                    CHNS_CUDA(cudaEventElapsedTime(&ms, ws->ev[6], ws->ev[7]));
+                    S.orth_ms += ms;
                     if (pc_pending) {
                         CHNS_CUDA(cudaEventElapsedTime(&ms, ws->ev[2], ws->ev[3]));
                         S.pc_ms += ms;
@@ -1361,6 +1408,7 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
             if (rnorm <= o->krylov_rtol * bnorm_s) break;
         }
         S.krylov_its += kry;
+        if (it < CHNS_HIST) S.krylov_hist[it] = kry;
         if (result != CHNS_OK) break;
         if (pin == 2) {
             // keep int p^{k+1} = int p^k: remove the mean of the pressure update (the

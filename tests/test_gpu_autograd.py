@@ -73,12 +73,15 @@ def test_residual_function_modes(chns):
     assert torch.allclose(t, ref, rtol=1e-12, atol=1e-14 * float(ref.abs().max()))
 
 
-def test_rollout_gradient_matches_central_differences(chns):
+@pytest.mark.parametrize("dim,cfg_name,dt,n_dirs,eps", [(2, "drop2d", 2e-3, 8, 1e-5),
+                                                       (3, "drop3d", 1e-3, 32, 1e-6)])
+def test_rollout_gradient_matches_central_differences(chns, dim, cfg_name, dt, n_dirs, eps):
     from paper_2009_06628_gb300.autograd import rollout
-    # 9 x 9 nodes x 5 fields: GMRES(256) is nearly a direct solve, so each implicit step is
-    # converged to rounding and central differences see a smooth map
-    gm, prm, cfg, U0 = small_problem(chns, level=3, dt=2e-3)
-    opts = chns.SolverOpts.make(rtol=1e-10, atol=1e-13, krylov_rtol=1e-12, precision=0, restart=256,
+    # level-3 meshes (9^d nodes): GMRES(256) with a 1e-12 Krylov tolerance nearly solves
+    # each linearisation exactly, so every implicit step is converged far below the
+    # finite-difference step and central differences see a smooth map
+    gm, prm, cfg, U0 = small_problem(chns, dim=dim, level=3, cfg_name=cfg_name, dt=dt)
+    opts = chns.SolverOpts.make(rtol=1e-12, atol=1e-13, krylov_rtol=1e-12, precision=0, restart=256,
                                 max_krylov=4000, max_newton=20)
     adj = chns.SolverOpts.make(krylov_rtol=1e-12, restart=256, max_krylov=4000, precision=0)
     n_steps, every = 20, 5
@@ -94,11 +97,9 @@ def test_rollout_gradient_matches_central_differences(chns):
     L = loss(phi0, Cn)
     L.backward()
     g_phi, g_cn = phi0.grad.clone(), float(Cn.grad)
-    # the implicit steps are converged to 1e-10 (row-equilibrated norm; the pressure rows
-    # set a rounding floor just below), so the central differences use eps = 1e-5, where
-    # solver noise (~1e-5 relative) and truncation (~eps^2) both stay below the bar
-    eps = 1e-5
-    dirs = synth.random_vectors(gm.N, 8, 77)
+    # each step's relative residual is below 1e-12, so solver noise in a central
+    # difference is ~1e-12 / eps and truncation ~eps^2, both below the 1e-4 bar
+    dirs = synth.random_vectors(gm.N, n_dirs, 77)
     with torch.no_grad():
         for i in range(dirs.shape[0]):
             v = torch.tensor(dirs[i], device="cuda")
@@ -107,7 +108,7 @@ def test_rollout_gradient_matches_central_differences(chns):
             fd = (lp - lm) / (2 * eps)
             ad = float((g_phi * v).sum())
             assert abs(fd - ad) <= 1e-4 * max(abs(fd), 1e-3), (i, fd, ad)
-        ec = 1e-5 * cfg["Cn"]
+        ec = eps * cfg["Cn"]
         fd = (float(loss(phi0, Cn + ec)) - float(loss(phi0, Cn - ec))) / (2 * ec)
         assert abs(fd - g_cn) <= 1e-4 * max(abs(fd), 1e-3), (fd, g_cn)
 
