@@ -49,6 +49,8 @@ struct SolverWS {
     // pressure Schur-complement approximation (FP32)
     float* ce = nullptr;     // E element coefficients
     float* kdinv = nullptr;  // N inverse diagonal
+    float* kbnd = nullptr;   // N bounds of the absolute row sums of the Schur Laplacian
+    unsigned int* kmax = nullptr;  // max_p kbnd[p] / diag[p] (float bits)
     float* cr = nullptr;     // N Chebyshev work vectors
     float* cx = nullptr;
     float* cd = nullptr;
@@ -92,6 +94,8 @@ void chns_solver_ws_free(SolverWS* ws) {
     cudaFree(ws->sc);
     cudaFree(ws->ce);
     cudaFree(ws->kdinv);
+    cudaFree(ws->kbnd);
+    cudaFree(ws->kmax);
     cudaFree(ws->cr);
     cudaFree(ws->cx);
     cudaFree(ws->cd);
@@ -150,6 +154,8 @@ chns_status ensure_ws(chns_mesh* m, int restart) {
     A((void**)&ws->sc, MAXSC * sizeof(double));
     A((void**)&ws->ce, (size_t)m->dm.E * sizeof(float));
     A((void**)&ws->kdinv, (size_t)m->dm.N * sizeof(float));
+    A((void**)&ws->kbnd, (size_t)m->dm.N * sizeof(float));
+    A((void**)&ws->kmax, sizeof(unsigned int));
     A((void**)&ws->cr, (size_t)m->dm.N * sizeof(float));
     A((void**)&ws->cx, (size_t)m->dm.N * sizeof(float));
     A((void**)&ws->cd, (size_t)m->dm.N * sizeof(float));
@@ -792,10 +798,13 @@ __device__ __forceinline__ void schur_corners(const DevMesh& m, int64_t e, int p
     }
 }
 
-// diagonal of the Schur Laplacian (constraint cross terms within a corner's parents
-// are dropped: it only scales the Chebyshev iteration)
+// Diagonal of the Schur Laplacian (constraint cross terms within a corner's parents
+// are dropped: it only scales the Chebyshev iteration) and, per node p, a bound on the
+// absolute row sum of the constrained operator: sum_q |K_pq| <= sum over the corners a
+// that map to p of w_ap sum_b |K_e[a][b]| (the constraint weights of a corner sum to 1).
 template <int D>
-__global__ void schur_diag_kernel(DevMesh m, const float* __restrict__ ce, float* __restrict__ dg) {
+__global__ void schur_diag_kernel(DevMesh m, const float* __restrict__ ce, float* __restrict__ dg,
+                                  float* __restrict__ bnd) {
     constexpr int NC = 1 << D;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= m.E) return;
@@ -805,8 +814,24 @@ __global__ void schur_diag_kernel(DevMesh m, const float* __restrict__ ce, float
     schur_corners<D>(m, e, par, np);
     for (int a = 0; a < NC; ++a) {
         const float w = np[a] == 1 ? 1.0f : (np[a] == 2 ? 0.5f : 0.25f);
-        for (int j = 0; j < np[a]; ++j) atomicAdd(dg + par[a][j], w * w * ch * c_Kref[a * NC + a]);
+        float rs = 0.0f;
+        for (int b = 0; b < NC; ++b) rs += fabsf(c_Kref[a * NC + b]);
+        for (int j = 0; j < np[a]; ++j) {
+            atomicAdd(dg + par[a][j], w * w * ch * c_Kref[a * NC + a]);
+            atomicAdd(bnd + par[a][j], w * ch * rs);
+        }
     }
+}
+
+// out = max_n bnd[n] dinv[n] (non-negative floats compare like their bit patterns)
+__global__ void gershgorin_max_kernel(const float* __restrict__ bnd, const float* __restrict__ dinv, int64_t N,
+                                      unsigned int* __restrict__ out) {
+    float v = 0.0f;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
+        v = fmaxf(v, bnd[n] * dinv[n]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(v));
 }
 
 // y += K_c x  (y zeroed by the caller)
@@ -1036,14 +1061,24 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
         }
         const int64_t N = m->dm.N;
         CHNS_CUDA(cudaMemsetAsync(ws->kdinv, 0, N * sizeof(float), c.s));
-        if (D == 2) { schur_diag_kernel<2><<<gE, 256, 0, c.s>>>(m->dm, ws->ce, ws->kdinv); chns_count_launches(1); }
-        else { schur_diag_kernel<3><<<gE, 256, 0, c.s>>>(m->dm, ws->ce, ws->kdinv); chns_count_launches(1); }
+        CHNS_CUDA(cudaMemsetAsync(ws->kbnd, 0, N * sizeof(float), c.s));
+        CHNS_CUDA(cudaMemsetAsync(ws->kmax, 0, sizeof(unsigned int), c.s));
+        if (D == 2) { schur_diag_kernel<2><<<gE, 256, 0, c.s>>>(m->dm, ws->ce, ws->kdinv, ws->kbnd); chns_count_launches(1); }
+        else { schur_diag_kernel<3><<<gE, 256, 0, c.s>>>(m->dm, ws->ce, ws->kdinv, ws->kbnd); chns_count_launches(1); }
         { recip_kernel<<<gN1, 256, 0, c.s>>>(ws->kdinv, N); chns_count_launches(1); }
-        // Every off-diagonal entry of the Q1 reference stiffness is <= 0, so Gershgorin
-        // bounds the spectrum of D^{-1} K by 2 (the Chebyshev interval must not cut the
-        // top of the spectrum, where the polynomial would amplify); 20% margin for the
-        // approximate diagonal at hanging nodes.
-        const double beta = 2.4;
+        // The Chebyshev interval must not cut the top of the spectrum of D^{-1} K, where
+        // the polynomial would amplify.  Gershgorin with the row-sum bounds gives it for
+        // any positive D: 2 on a uniform mesh (off-diagonal stiffness entries are <= 0),
+        // more where hanging constraints fold positive weights into a row.
+        { gershgorin_max_kernel<<<c.g, 256, 0, c.s>>>(ws->kbnd, ws->kdinv, N, ws->kmax); chns_count_launches(1); }
+        unsigned int kbits = 0;
+        CHNS_CUDA(cudaMemcpyAsync(&ws->hsc[0], ws->kmax, sizeof(unsigned int), cudaMemcpyDeviceToHost, c.s));
+        CHNS_CUDA(cudaStreamSynchronize(c.s));
+        std::memcpy(&kbits, &ws->hsc[0], sizeof(unsigned int));
+        float kb;
+        std::memcpy(&kb, &kbits, sizeof(float));
+        if (!(kb > 0.0f) || !std::isfinite(kb)) { chns_set_error("pressure Schur spectrum bound is not finite"); return CHNS_ENAN; }
+        const double beta = 1.01 * (double)kb;
         const double nside = std::ldexp(1.0, m->max_level);
         const double ratio = std::max(16.0, nside * nside / 8.0);
         const double alpha = beta / ratio;
