@@ -263,7 +263,7 @@ def run_trajectory(args):
     chns.initial_mu(gm, prm, U0)
     dof = U0.numel()
     kw = dict(rtol=1e-9, atol=1e-14, krylov_rtol=1e-3, restart=args.restart, max_krylov=args.max_krylov,
-              pc_type=args.pc_type, pc_degree=8)
+              pc_type=args.pc_type, pc_degree=16)
     o32 = chns.SolverOpts.make(precision=1, **kw)
     o64 = chns.SolverOpts.make(precision=0, **kw)
     fields = {"v": slice(0, d), "p": slice(d, d + 1), "phi": slice(d + 1, d + 2), "mu": slice(d + 2, d + 3)}
@@ -356,7 +356,7 @@ def main():
     chns.initial_mu(gm, prm, U0)
     dof = U0.numel()
     opts = chns.SolverOpts.make(rtol=1e-9, atol=1e-14, krylov_rtol=1e-3, precision=1, restart=30, max_krylov=2000,
-                                pc_type=1, pc_degree=8)
+                                pc_type=1, pc_degree=16)
     U1 = torch.empty_like(U0)
     for _ in range(args.warmup):
         chns.newton_step(gm, prm, opts, U0, U1)
@@ -410,7 +410,7 @@ def main():
     newton = {"mixed_ms": t_ms / args.steps, "mixed_stats": stats[-1]}
     if not args.no_fp64:
         o64 = chns.SolverOpts.make(rtol=1e-9, atol=1e-14, krylov_rtol=1e-3, precision=0, restart=30, max_krylov=2000,
-                                   pc_type=1, pc_degree=8)
+                                   pc_type=1, pc_degree=16)
         U64 = torch.empty_like(U0)
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)

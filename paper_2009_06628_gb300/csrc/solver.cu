@@ -900,10 +900,12 @@ void mref_host(int D, float* Mr) {
         }
 }
 
-// y += (alpha M + beta K) x, or its diagonal (DIAG), on the Q1 space with constraints
+// y += (alpha M + beta K) x, or its diagonal (DIAG), on the Q1 space with constraints;
+// DIAG also accumulates into bnd the absolute-row-sum bounds used for the Gershgorin
+// top of the spectrum (as for the pressure Schur Laplacian)
 template <int D, bool DIAG>
 __global__ void mk_kernel(DevMesh m, float span, float alpha, float beta, const float* __restrict__ x,
-                          float* __restrict__ y) {
+                          float* __restrict__ y, float* __restrict__ bnd = nullptr) {
     constexpr int NC = 1 << D;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= m.E) return;
@@ -917,7 +919,12 @@ __global__ void mk_kernel(DevMesh m, float span, float alpha, float beta, const 
         for (int a = 0; a < NC; ++a) {
             const float w = np[a] == 1 ? 1.0f : (np[a] == 2 ? 0.5f : 0.25f);
             const float v = am * c_Mref[a * NC + a] + bk * c_Kref[a * NC + a];
-            for (int j = 0; j < np[a]; ++j) atomicAdd(y + par[a][j], w * w * v);
+            float rs = 0.0f;
+            for (int b = 0; b < NC; ++b) rs += fabsf(am * c_Mref[a * NC + b] + bk * c_Kref[a * NC + b]);
+            for (int j = 0; j < np[a]; ++j) {
+                atomicAdd(y + par[a][j], w * w * v);
+                if (bnd) atomicAdd(bnd + par[a][j], w * rs);
+            }
         }
         return;
     }
@@ -1140,13 +1147,23 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
         else { ch_nodal_kernel<double><<<gN1, 256, 0, c.s>>>(N, NF, D + 1, (const double*)Uo_any, (const double*)Un_any, m->d_nmass, ws->ch_psi2, ws->ch_ml); chns_count_launches(1); }
         ws->ch_eps = (float)std::sqrt(p->dt * p->Cn / (2.0 * p->Pe));
         CHNS_CUDA(cudaMemsetAsync(ws->ch_dinv, 0, N * sizeof(float), c.s));
-        if (D == 2) { mk_kernel<2, true><<<gE, 256, 0, c.s>>>(m->dm, span, 1.0f, ws->ch_eps, nullptr, ws->ch_dinv); chns_count_launches(1); }
-        else { mk_kernel<3, true><<<gE, 256, 0, c.s>>>(m->dm, span, 1.0f, ws->ch_eps, nullptr, ws->ch_dinv); chns_count_launches(1); }
+        CHNS_CUDA(cudaMemsetAsync(ws->kbnd, 0, N * sizeof(float), c.s));
+        CHNS_CUDA(cudaMemsetAsync(ws->kmax, 0, sizeof(unsigned int), c.s));
+        if (D == 2) { mk_kernel<2, true><<<gE, 256, 0, c.s>>>(m->dm, span, 1.0f, ws->ch_eps, nullptr, ws->ch_dinv, ws->kbnd); chns_count_launches(1); }
+        else { mk_kernel<3, true><<<gE, 256, 0, c.s>>>(m->dm, span, 1.0f, ws->ch_eps, nullptr, ws->ch_dinv, ws->kbnd); chns_count_launches(1); }
         { recip_kernel<<<gN1, 256, 0, c.s>>>(ws->ch_dinv, N); chns_count_launches(1); }
+        // top of the spectrum of D^{-1}(M + eps K): Gershgorin with the row-sum bounds
+        // (3.375 for the Q1 mass on a uniform 3D mesh, 2 for the stiffness)
+        { gershgorin_max_kernel<<<c.g, 256, 0, c.s>>>(ws->kbnd, ws->ch_dinv, N, ws->kmax); chns_count_launches(1); }
         CHNS_CUDA(cudaGetLastError());
-        // spectrum of D^{-1}(M + eps K) lies in (0, 3.375] for Q1 (Gershgorin; mass and
-        // stiffness row ratios); Chebyshev interval [0.05, 4]
-        const double beta = 4.0, alpha = 0.05;
+        unsigned int kbits = 0;
+        CHNS_CUDA(cudaMemcpyAsync(&ws->hsc[0], ws->kmax, sizeof(unsigned int), cudaMemcpyDeviceToHost, c.s));
+        CHNS_CUDA(cudaStreamSynchronize(c.s));
+        std::memcpy(&kbits, &ws->hsc[0], sizeof(unsigned int));
+        float kb;
+        std::memcpy(&kb, &kbits, sizeof(float));
+        if (!(kb > 0.0f) || !std::isfinite(kb)) { chns_set_error("Cahn-Hilliard block spectrum bound is not finite"); return CHNS_ENAN; }
+        const double beta = 1.01 * (double)kb, alpha = 0.05;
         const double theta = 0.5 * (beta + alpha), delta = 0.5 * (beta - alpha), sigma = theta / delta;
         ws->ch_c1.assign(CH_DEG, 0.0f);
         ws->ch_c2.assign(CH_DEG, 0.0f);
