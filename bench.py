@@ -171,37 +171,44 @@ def aggregate_replicas(t_ms, work, dist=None, device="cpu"):
     return float(t), float(w)
 
 
-def layer_workload():
+def layer_workload(min_level=5, max_level=10):
     """Two-layer (Rayleigh-Taylor-shaped) workload: heavy fluid on top (density ratio 3),
     interface z = 0.5 + 0.05 cos(2 pi x + phase) with a seeded phase; octree levels 5-10
-    refined in a band graded so that it is 2:1 balanced by construction (26.1M elements)."""
+    refined in a band graded so that it is 2:1 balanced by construction (26.1M elements).
+    The reduced version (levels 4-8) keeps Cn / h_min = 2.56 with Cn = 0.01."""
     rng = np.random.default_rng(5)
     phase = float(rng.uniform(0.0, 2.0 * np.pi))
     dist = synth.layer_distance(0.5, 0.05, 1.0, phase)
-    leaves = synth.graded_band_leaves(DIM, 5, 10, dist, 0.0, grade=3.0)
+    leaves = synth.graded_band_leaves(DIM, min_level, max_level, dist, 0.0, grade=3.0)
     cfg = synth.config_params("layer3d")
-    return leaves, 10, cfg, phase
+    cfg["Cn"] *= 2.0 ** (10 - max_level)
+    return leaves, max_level, cfg, phase
 
 
-def twodrops_workload():
+def twodrops_workload(min_level=4, max_level=9):
     """Two drops (radii 0.12, 0.15, centres 0.35 apart, seeded orientation), octree
-    levels 4-9 refined within 3 Cn of the interfaces, 2:1 balanced (2.49M elements)."""
+    levels 4-9 refined within 3 Cn of the interfaces, 2:1 balanced (2.49M elements).
+    The reduced version (levels 3-7, Cn = 0.02, band 0.03) has 101,368 elements."""
     cfg = synth.config_params("twodrops3d")
     centers, radii = synth.two_drops(3)
-    leaves = synth.sphere_band_leaves(DIM, 4, 9, centers, radii, 3 * cfg["Cn"])
-    return leaves, 9, cfg, (centers, radii)
+    if max_level == 9:
+        leaves = synth.sphere_band_leaves(DIM, min_level, max_level, centers, radii, 3 * cfg["Cn"])
+    else:
+        cfg["Cn"] = 0.02
+        leaves = synth.sphere_band_leaves(DIM, min_level, max_level, centers, radii, 0.03)
+    return leaves, max_level, cfg, (centers, radii)
 
 
 def workload_mesh(chns, args):
     """(device mesh, parameters, host state) of the workload chosen by --mesh / --level."""
-    if args.mesh == "layer":
-        leaves, level, cfg, phase = layer_workload()
+    if args.mesh in ("layer", "layer_l8"):
+        leaves, level, cfg, phase = layer_workload(*((4, 8) if args.mesh == "layer_l8" else (5, 10)))
         gm = chns.Mesh(DIM, level, leaves)
         x = gm.node_x()
         U = np.zeros((gm.N, DIM + 3))
         U[:, DIM + 1] = synth.layer_phi(x, 0.5, 0.05, 1.0, phase, cfg["Cn"])
-    elif args.mesh == "twodrops":
-        leaves, level, cfg, (centers, radii) = twodrops_workload()
+    elif args.mesh in ("twodrops", "twodrops_l7"):
+        leaves, level, cfg, (centers, radii) = twodrops_workload(*((3, 7) if args.mesh == "twodrops_l7" else (4, 9)))
         gm = chns.Mesh(DIM, level, leaves)
         x = gm.node_x()
         U = np.zeros((gm.N, DIM + 3))
@@ -319,7 +326,7 @@ def main():
     ap.add_argument("--profile", choices=["jvp32", "jvp64", "residual", "vjp"],
                     help="run only this kernel --reps times on a uniform mesh of --level (for ncu)")
     ap.add_argument("--level", type=int, default=LEVEL)
-    ap.add_argument("--mesh", choices=["uniform", "twodrops", "layer"], default="uniform")
+    ap.add_argument("--mesh", choices=["uniform", "twodrops", "twodrops_l7", "layer", "layer_l8"], default="uniform")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--run", action="store_true",
                     help="multi-step Newton run on --mesh (mixed, and FP64 for --fp64-steps) instead of the bench")
