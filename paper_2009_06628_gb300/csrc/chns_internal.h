@@ -19,11 +19,6 @@ struct DevMesh {
     const uint8_t* nflag;   // N node flags, bit 0: on the domain boundary
     const int32_t* bnodes;  // NB boundary node indices
     const int32_t* anchor;  // E * dim element anchors (units of the finest cell)
-    // node -> element-corner incidence (CSR over independent nodes): every corner that
-    // contributes to node p, as (element << 5) | (corner << 2) | weight code (0: 1,
-    // 1: 1/2, 2: 1/4), elements ascending; for node-parallel scalar operators
-    const int64_t* inc_ptr; // N + 1
-    const uint32_t* inc;
     int32_t max_level;
     double lo, hi;
 };
@@ -41,8 +36,6 @@ struct chns_mesh {
     uint8_t* d_nflag = nullptr;
     int32_t* d_bnodes = nullptr;
     int32_t* d_anchor = nullptr;
-    int64_t* d_inc_ptr = nullptr;
-    uint32_t* d_inc = nullptr;
     double* d_nmass = nullptr;       // integral of each node's basis function
     double volume = 0.0;             // |Omega|
     // reduction workspace: per-block partial sums and a flag word

@@ -275,42 +275,6 @@ extern "C" chns_status chns_mesh_create(int32_t dim, int32_t max_level, int64_t 
             }
         }
     }
-    // node -> element-corner incidence (elements ascending within a node)
-    if (E >= ((int64_t)1 << 27)) {
-        chns_mesh_destroy(m);
-        chns_set_error("more than 2^27 elements");
-        return CHNS_EINVAL;
-    }
-    std::vector<int64_t> inc_ptr(N + 1, 0);
-    for (int64_t e = 0; e < E; ++e)
-        for (int c = 0; c < nc; ++c) {
-            const int32_t ent = e2n[(size_t)e * nc + c];
-            if (ent >= 0) {
-                inc_ptr[ent + 1]++;
-            } else {
-                const int32_t* hp = &hang[(size_t)(-ent - 1) * 4];
-                const int np = hp[2] < 0 ? 2 : 4;
-                for (int j = 0; j < np; ++j) inc_ptr[hp[j] + 1]++;
-            }
-        }
-    for (int64_t n = 0; n < N; ++n) inc_ptr[n + 1] += inc_ptr[n];
-    std::vector<uint32_t> inc((size_t)std::max<int64_t>(inc_ptr[N], 1));
-    {
-        std::vector<int64_t> cur(inc_ptr.begin(), inc_ptr.end() - 1);
-        for (int64_t e = 0; e < E; ++e)
-            for (int c = 0; c < nc; ++c) {
-                const int32_t ent = e2n[(size_t)e * nc + c];
-                const uint32_t base = ((uint32_t)e << 5) | ((uint32_t)c << 2);
-                if (ent >= 0) {
-                    inc[(size_t)cur[ent]++] = base;
-                } else {
-                    const int32_t* hp = &hang[(size_t)(-ent - 1) * 4];
-                    const int np = hp[2] < 0 ? 2 : 4;
-                    const uint32_t wc = np == 2 ? 1u : 2u;
-                    for (int j = 0; j < np; ++j) inc[(size_t)cur[hp[j]]++] = base | wc;
-                }
-            }
-    }
     std::vector<int32_t> anchor32((size_t)E * d);
     for (size_t i = 0; i < anchor32.size(); ++i) anchor32[i] = (int32_t)anchor[i];
     std::vector<int8_t> level8(E);
@@ -323,9 +287,7 @@ extern "C" chns_status chns_mesh_create(int32_t dim, int32_t max_level, int64_t 
         (st = dev_upload(&m->d_nflag, nflag)) != CHNS_OK ||
         (st = dev_upload(&m->d_bnodes, bnodes)) != CHNS_OK ||
         (st = dev_upload(&m->d_anchor, anchor32)) != CHNS_OK ||
-        (st = dev_upload(&m->d_nmass, nmass)) != CHNS_OK ||
-        (st = dev_upload(&m->d_inc_ptr, inc_ptr)) != CHNS_OK ||
-        (st = dev_upload(&m->d_inc, inc)) != CHNS_OK) {
+        (st = dev_upload(&m->d_nmass, nmass)) != CHNS_OK) {
         chns_mesh_destroy(m);
         return st;
     }
@@ -352,8 +314,6 @@ extern "C" chns_status chns_mesh_create(int32_t dim, int32_t max_level, int64_t 
     dm.nflag = m->d_nflag;
     dm.bnodes = m->d_bnodes;
     dm.anchor = m->d_anchor;
-    dm.inc_ptr = m->d_inc_ptr;
-    dm.inc = m->d_inc;
     dm.max_level = L;
     dm.lo = lo;
     dm.hi = hi;
@@ -373,8 +333,6 @@ extern "C" void chns_mesh_destroy(chns_mesh* m) {
     cudaFree(m->d_nflag);
     cudaFree(m->d_bnodes);
     cudaFree(m->d_anchor);
-    cudaFree(m->d_inc_ptr);
-    cudaFree(m->d_inc);
     cudaFree(m->d_nmass);
     cudaFree(m->d_partials);
     cudaFree(m->d_flags);

@@ -1021,55 +1021,6 @@ __global__ void cheb_final_kernel(int64_t N, int NF, int f, const float* __restr
     if (n < N) z[(size_t)n * NF + f] = (TO)(x[n] + d[n]);
 }
 
-// One Chebyshev step of the pressure Schur approximation with the matvec done node by
-// node through the node -> element-corner incidence (a gather, so no atomics and no
-// separate update launch): y_p = sum over the corners folded into p of w (K_e d)_corner,
-// then x += d, r -= y, d' = c1 d + c2 dinv r.  d is read from din and written to dout
-// (other threads gather din); r and x are touched by their own node only.
-template <int D>
-__global__ void __launch_bounds__(256) schur_cheb_kernel(DevMesh m, float span, const float* __restrict__ ce,
-                                                          const float* __restrict__ din, float* __restrict__ dout,
-                                                          float* __restrict__ r, float* __restrict__ x,
-                                                          const float* __restrict__ dinv, float c1, float c2) {
-    constexpr int NC = 1 << D;
-    __shared__ float sK[NC * NC];
-    for (int i = threadIdx.x; i < NC * NC; i += blockDim.x) sK[i] = c_Kref[i];
-    __syncthreads();
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= m.N) return;
-    float y = 0.0f;
-    const int64_t k1 = m.inc_ptr[p + 1];
-    for (int64_t k = m.inc_ptr[p]; k < k1; ++k) {
-        const uint32_t u = m.inc[k];
-        const int64_t e = (int64_t)(u >> 5);
-        const int a = (int)((u >> 2) & 7u);
-        const uint32_t wc = u & 3u;
-        const float w = wc == 0u ? 1.0f : (wc == 1u ? 0.5f : 0.25f);
-        const float h = ldexpf(span, -(int)m.level[e]);
-        const float ch = ce[e] * (D == 2 ? 1.0f : h);
-        float s = 0.0f;
-#pragma unroll
-        for (int b = 0; b < NC; ++b) {
-            const int ent = m.e2n[e * NC + b];
-            float xb;
-            if (ent >= 0) {
-                xb = __ldg(din + ent);
-            } else {
-                const int4 hp = reinterpret_cast<const int4*>(m.hang)[-ent - 1];
-                xb = hp.z < 0 ? 0.5f * (__ldg(din + hp.x) + __ldg(din + hp.y))
-                              : 0.25f * (__ldg(din + hp.x) + __ldg(din + hp.y) + __ldg(din + hp.z) + __ldg(din + hp.w));
-            }
-            s += sK[a * NC + b] * xb;
-        }
-        y += w * ch * s;
-    }
-    const float dk = din[p];
-    x[p] += dk;
-    const float rn = r[p] - y;
-    r[p] = rn;
-    dout[p] = c1 * dk + c2 * dinv[p] * rn;
-}
-
 // y = dinv .* (K_c x): one power-iteration step
 __global__ void scale_by_kernel(const float* __restrict__ dinv, float* __restrict__ y, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1158,16 +1109,12 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
         using TO = std::remove_pointer_t<decltype(zout)>;
         const int64_t N = m->dm.N;
         { cheb_init_kernel<TI><<<gN1, 256, 0, c.s>>>(N, NF, D, vin, ws->kdinv, ws->cr, ws->cx, ws->cd, ws->cy, ws->cheb_inv_theta); chns_count_launches(1); }
-        // search direction ping-pongs between cd and cy (the gather reads the old one)
-        const float span = (float)(m->dm.hi - m->dm.lo);
-        float* dA = ws->cd;
-        float* dB = ws->cy;
         for (int k = 0; k + 1 < o->pc_degree; ++k) {
-            if (D == 2) { schur_cheb_kernel<2><<<gN1, 256, 0, c.s>>>(m->dm, span, ws->ce, dA, dB, ws->cr, ws->cx, ws->kdinv, ws->cheb_c1[k], ws->cheb_c2[k]); chns_count_launches(1); }
-            else { schur_cheb_kernel<3><<<gN1, 256, 0, c.s>>>(m->dm, span, ws->ce, dA, dB, ws->cr, ws->cx, ws->kdinv, ws->cheb_c1[k], ws->cheb_c2[k]); chns_count_launches(1); }
-            std::swap(dA, dB);
+            if (D == 2) { schur_matvec_kernel<2><<<gE, 256, 0, c.s>>>(m->dm, ws->ce, ws->cd, ws->cy); chns_count_launches(1); }
+            else { schur_matvec_kernel<3><<<gE, 256, 0, c.s>>>(m->dm, ws->ce, ws->cd, ws->cy); chns_count_launches(1); }
+            { cheb_step_kernel<<<gN1, 256, 0, c.s>>>(N, ws->kdinv, ws->cr, ws->cx, ws->cd, ws->cy, ws->cheb_c1[k], ws->cheb_c2[k]); chns_count_launches(1); }
         }
-        { cheb_final_kernel<TO><<<gN1, 256, 0, c.s>>>(N, NF, D, ws->cx, dA, zout); chns_count_launches(1); }
+        { cheb_final_kernel<TO><<<gN1, 256, 0, c.s>>>(N, NF, D, ws->cx, ws->cd, zout); chns_count_launches(1); }
         CHNS_CUDA(cudaGetLastError());
         return CHNS_OK;
     };
