@@ -83,7 +83,9 @@ typedef struct {
  * S = 1/|diag J| at U^0 (every field weighed by its own scale; the pressure rows carry
  * coefficients of order tau/We).  Newton stops when ||S R||_2 <= rtol * ||S R(U^0)||_2 or
  * ||S R||_2 <= atol.  Krylov: GMRES(restart) on S J M^{-1} (M: nodal block-Jacobi,
- * right preconditioning) to relative tolerance krylov_rtol, at most max_krylov
+ * right preconditioning) to relative tolerance eta = max(krylov_rtol, min(0.5,
+ * 0.1 * target / ||S R||)) with target = max(atol, rtol ||S R(U^0)||) (the last linear
+ * solve is not driven further than the Newton target needs), at most max_krylov
  * iterations per Newton iteration. */
 typedef struct {
     double rtol, atol, krylov_rtol;

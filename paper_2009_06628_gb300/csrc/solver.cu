@@ -49,6 +49,18 @@ struct SolverWS {
     // pressure Schur-complement approximation (FP32)
     float* ce = nullptr;     // E element coefficients
     float* kdinv = nullptr;  // N inverse diagonal
+    // CUDA graphs of the pressure Schur apply (2 + 2 (degree - 1) launches), captured on
+    // a private stream per (input, output, output type) and Chebyshev set-up
+    struct SchurGraph {
+        cudaGraphExec_t exec = nullptr;
+        const void* vin = nullptr;
+        void* zout = nullptr;
+        size_t to = 0;
+        int gen = -1;
+    } sgraph[4];
+    cudaStream_t cap = nullptr;
+    int schur_gen = 0;
+    bool no_graphs = false;
     float* kbnd = nullptr;   // N bounds of the absolute row sums of the Schur Laplacian
     unsigned int* kmax = nullptr;  // max_p kbnd[p] / diag[p] (float bits)
     float* cr = nullptr;     // N Chebyshev work vectors
@@ -73,6 +85,9 @@ struct SolverWS {
 
 void chns_solver_ws_free(SolverWS* ws) {
     if (!ws) return;
+    for (auto& g : ws->sgraph)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (ws->cap) cudaStreamDestroy(ws->cap);
     cudaFree(ws->V);
     cudaFree(ws->w);
     cudaFree(ws->R);
@@ -1101,6 +1116,7 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
             rho = rn;
         }
         ws->cheb_inv_theta = (float)(1.0 / theta);
+        ws->schur_gen++;   // captured applies hold the old coefficients
         return CHNS_OK;
     };
     // z_p = (Chebyshev approximation of S^{-1}) v_p, strided input and output
@@ -1108,13 +1124,58 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
         using TI = std::remove_const_t<std::remove_pointer_t<decltype(vin)>>;
         using TO = std::remove_pointer_t<decltype(zout)>;
         const int64_t N = m->dm.N;
-        { cheb_init_kernel<TI><<<gN1, 256, 0, c.s>>>(N, NF, D, vin, ws->kdinv, ws->cr, ws->cx, ws->cd, ws->cy, ws->cheb_inv_theta); chns_count_launches(1); }
-        for (int k = 0; k + 1 < o->pc_degree; ++k) {
-            if (D == 2) { schur_matvec_kernel<2><<<gE, 256, 0, c.s>>>(m->dm, ws->ce, ws->cd, ws->cy); chns_count_launches(1); }
-            else { schur_matvec_kernel<3><<<gE, 256, 0, c.s>>>(m->dm, ws->ce, ws->cd, ws->cy); chns_count_launches(1); }
-            { cheb_step_kernel<<<gN1, 256, 0, c.s>>>(N, ws->kdinv, ws->cr, ws->cx, ws->cd, ws->cy, ws->cheb_c1[k], ws->cheb_c2[k]); chns_count_launches(1); }
+        // the apply is 2 + 2 (degree - 1) short launches: replayed from a CUDA graph
+        auto enqueue = [&](cudaStream_t st) {
+            cheb_init_kernel<TI><<<gN1, 256, 0, st>>>(N, NF, D, vin, ws->kdinv, ws->cr, ws->cx, ws->cd, ws->cy, ws->cheb_inv_theta);
+            for (int k = 0; k + 1 < o->pc_degree; ++k) {
+                if (D == 2) schur_matvec_kernel<2><<<gE, 256, 0, st>>>(m->dm, ws->ce, ws->cd, ws->cy);
+                else schur_matvec_kernel<3><<<gE, 256, 0, st>>>(m->dm, ws->ce, ws->cd, ws->cy);
+                cheb_step_kernel<<<gN1, 256, 0, st>>>(N, ws->kdinv, ws->cr, ws->cx, ws->cd, ws->cy, ws->cheb_c1[k], ws->cheb_c2[k]);
+            }
+            cheb_final_kernel<TO><<<gN1, 256, 0, st>>>(N, NF, D, ws->cx, ws->cd, zout);
+        };
+        const int nk = 2 + 2 * (o->pc_degree - 1);
+        if (!ws->no_graphs) {
+            SolverWS::SchurGraph* hit = nullptr;
+            for (auto& g : ws->sgraph)
+                if (g.exec && g.gen == ws->schur_gen && g.vin == (const void*)vin && g.zout == (void*)zout &&
+                    g.to == sizeof(TO))
+                    hit = &g;
+            if (!hit) {
+                SolverWS::SchurGraph* slot = &ws->sgraph[0];
+                for (auto& g : ws->sgraph)
+                    if (!g.exec || g.gen != ws->schur_gen) { slot = &g; break; }
+                cudaGraphExec_t ex = nullptr;
+                cudaGraph_t gr = nullptr;
+                bool ok = ws->cap || cudaStreamCreateWithFlags(&ws->cap, cudaStreamNonBlocking) == cudaSuccess;
+                if (ok) ok = cudaStreamBeginCapture(ws->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+                if (ok) {
+                    enqueue(ws->cap);
+                    ok = cudaStreamEndCapture(ws->cap, &gr) == cudaSuccess && gr != nullptr;
+                    if (ok) ok = cudaGraphInstantiate(&ex, gr, 0) == cudaSuccess;
+                    if (gr) cudaGraphDestroy(gr);
+                }
+                if (!ok) {
+                    (void)cudaGetLastError();   // capture unavailable: launch directly from now on
+                    ws->no_graphs = true;
+                } else {
+                    if (slot->exec) cudaGraphExecDestroy(slot->exec);
+                    slot->exec = ex;
+                    slot->vin = (const void*)vin;
+                    slot->zout = (void*)zout;
+                    slot->to = sizeof(TO);
+                    slot->gen = ws->schur_gen;
+                    hit = slot;
+                }
+            }
+            if (hit) {
+                CHNS_CUDA(cudaGraphLaunch(hit->exec, c.s));
+                chns_count_launches(nk);
+                return CHNS_OK;
+            }
         }
-        { cheb_final_kernel<TO><<<gN1, 256, 0, c.s>>>(N, NF, D, ws->cx, ws->cd, zout); chns_count_launches(1); }
+        enqueue(c.s);
+        chns_count_launches(nk);
         CHNS_CUDA(cudaGetLastError());
         return CHNS_OK;
     };
@@ -1296,6 +1357,10 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
             rnorm = std::sqrt(bb);
         }
         const double bnorm_s = rnorm;
+        // forcing term: krylov_rtol, relaxed once the Newton target is near (a solve
+        // below a tenth of what the target needs is wasted)
+        const double target = std::max(o->atol, o->rtol * r0);
+        const double eta = std::max(o->krylov_rtol, std::min(0.5, 0.1 * target / rn));
         while (true) {
             // V0 = r / ||r||
             double beta = rnorm;
@@ -1401,7 +1466,7 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                 rnorm = std::fabs(gv[j + 1]);
                 if (hn > 0.0)
                     { axpby_kernel<<<c.g, 256, 0, c.s>>>(1.0 / hn, ws->w, 0.0, ws->V + (size_t)(j + 1) * c.n, c.n); chns_count_launches(1); }
-                if (rnorm <= o->krylov_rtol * bnorm_s || hn == 0.0) {
+                if (rnorm <= eta * bnorm_s || hn == 0.0) {
                     ++j;
                     ++kry;
                     done = true;
@@ -1457,7 +1522,7 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                 CHNS_CUDA(cudaEventElapsedTime(&ms, ws->ev[0], ws->ev[1]));
                 S.jvp_ms += ms;
             }
-            if (rnorm <= o->krylov_rtol * bnorm_s) break;
+            if (rnorm <= eta * bnorm_s) break;
         }
         S.krylov_its += kry;
         if (it < CHNS_HIST) S.krylov_hist[it] = kry;
