@@ -850,101 +850,30 @@ __global__ void gershgorin_max_kernel(const float* __restrict__ bnd, const float
 }
 
 // y += K_c x  (y zeroed by the caller)
-// y += K_c x  (y zeroed by the caller).  One thread per element, blocks of 256.  The 2^d
-// elements of an aligned group of lanes that form one complete family (same level,
-// children 0..2^d-1 of one parent, in Morton order) first sum their corner rows in
-// shared memory over the 3^d points of the family, then issue 3^d global atomics
-// instead of 4^d; other elements scatter directly.  Atomics bound this kernel.
 template <int D>
-__global__ void __launch_bounds__(256) schur_matvec_kernel(DevMesh m, const float* __restrict__ ce,
-                                                           const float* __restrict__ x, float* __restrict__ y) {
-    constexpr int NC = 1 << D, NP = (D == 2) ? 9 : 27;
-    __shared__ float sacc[256 / NC][NP];
+__global__ void schur_matvec_kernel(DevMesh m, const float* __restrict__ ce, const float* __restrict__ x,
+                                    float* __restrict__ y) {
+    constexpr int NC = 1 << D;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = e < m.E;
-    const int lane = threadIdx.x & 31, gi = threadIdx.x % NC, grp = threadIdx.x / NC;
-    const int lead = lane - gi;                             // first lane of this family group
-    const unsigned gmask = ((1u << NC) - 1u) << lead;
-    int lvl = valid ? (int)m.level[e] : -1;
-    int anc[3] = {0, 0, 0};
-    if (valid)
-        for (int k = 0; k < D; ++k) anc[k] = m.anchor[e * D + k];
-    // complete family: same level as the group's first element, anchor = first anchor +
-    // child offset, first anchor aligned to the parent size
-    const int lvl0 = __shfl_sync(0xffffffffu, lvl, lead);
-    bool fam = valid && lvl == lvl0 && lvl > 0;
-    {
-        const int sz = fam ? (1 << (m.max_level - lvl)) : 1;
-        for (int k = 0; k < D; ++k) {
-            const int a0 = __shfl_sync(0xffffffffu, anc[k], lead);
-            fam = fam && (a0 % (2 * sz) == 0) && (anc[k] == a0 + (((gi >> k) & 1) ? sz : 0));
-        }
-    }
-    const bool family = (__ballot_sync(0xffffffffu, fam) & gmask) == gmask;
-    float r[NC];
+    if (e >= m.E) return;
+    const float h = (float)ldexp(m.hi - m.lo, -(int)m.level[e]);
+    const float ch = ce[e] * (D == 2 ? 1.0f : h);
     int par[NC][4], np[NC];
-    if (valid) {
-        const float h = (float)ldexp(m.hi - m.lo, -lvl);
-        const float ch = ce[e] * (D == 2 ? 1.0f : h);
-        schur_corners<D>(m, e, par, np);
-        float xl[NC];
-        for (int a = 0; a < NC; ++a) {
-            const float w = np[a] == 1 ? 1.0f : (np[a] == 2 ? 0.5f : 0.25f);
-            float s = 0.0f;
-            for (int j = 0; j < np[a]; ++j) s += w * __ldg(x + par[a][j]);
-            xl[a] = s;
-        }
-        for (int a = 0; a < NC; ++a) {
-            float s = 0.0f;
-#pragma unroll
-            for (int b = 0; b < NC; ++b) s += c_Kref[a * NC + b] * xl[b];
-            r[a] = s * ch;
-        }
-    }
-    if (!family) {
-        if (valid)
-            for (int a = 0; a < NC; ++a) {
-                const float w = np[a] == 1 ? 1.0f : (np[a] == 2 ? 0.5f : 0.25f);
-                for (int j = 0; j < np[a]; ++j) atomicAdd(y + par[a][j], w * r[a]);
-            }
-        return;
-    }
-    // family path (all NC lanes of the group are here): point index of child c, corner a
-    // on the 3^d grid of the parent is sum_k (c_k + a_k) 3^k
-    float* acc = sacc[grp];
-    for (int t = gi; t < NP; t += NC) acc[t] = 0.0f;
-    __syncwarp(gmask);
+    schur_corners<D>(m, e, par, np);
+    float xl[NC];
     for (int a = 0; a < NC; ++a) {
-        int t = 0, p3 = 1;
-        for (int k = 0; k < D; ++k, p3 *= 3) t += (((gi >> k) & 1) + ((a >> k) & 1)) * p3;
-        atomicAdd(&acc[t], r[a]);
+        const float w = np[a] == 1 ? 1.0f : (np[a] == 2 ? 0.5f : 0.25f);
+        float s = 0.0f;
+        for (int j = 0; j < np[a]; ++j) s += w * __ldg(x + par[a][j]);
+        xl[a] = s;
     }
-    __syncwarp(gmask);
-    const int64_t e0 = e - gi;
-    for (int t = gi; t < NP; t += NC) {
-        // the point's owner: child c and corner a with c_k + a_k = t_k (c_k = 1 only for t_k = 2)
-        int c = 0, a = 0, tt = t;
-        for (int k = 0; k < D; ++k, tt /= 3) {
-            const int tk = tt % 3;
-            if (tk == 2) c |= 1 << k;
-            if (tk >= 1) a |= 1 << k;
-        }
-        const float v = acc[t];
-        const int ent = m.e2n[(e0 + c) * NC + a];
-        if (ent >= 0) {
-            atomicAdd(y + ent, v);
-        } else {
-            const int4 hp = reinterpret_cast<const int4*>(m.hang)[-ent - 1];
-            if (hp.z < 0) {
-                atomicAdd(y + hp.x, 0.5f * v);
-                atomicAdd(y + hp.y, 0.5f * v);
-            } else {
-                atomicAdd(y + hp.x, 0.25f * v);
-                atomicAdd(y + hp.y, 0.25f * v);
-                atomicAdd(y + hp.z, 0.25f * v);
-                atomicAdd(y + hp.w, 0.25f * v);
-            }
-        }
+    for (int a = 0; a < NC; ++a) {
+        float s = 0.0f;
+#pragma unroll
+        for (int b = 0; b < NC; ++b) s += c_Kref[a * NC + b] * xl[b];
+        s *= ch;
+        const float w = np[a] == 1 ? 1.0f : (np[a] == 2 ? 0.5f : 0.25f);
+        for (int j = 0; j < np[a]; ++j) atomicAdd(y + par[a][j], w * s);
     }
 }
 
