@@ -229,7 +229,8 @@ chns_status chns_mass_solve(const chns_mesh* mesh, const double* rhs, double* x,
 chns_status chns_mass_static(const chns_mesh* mesh, const double* U, double* out, void* stream);
 
 /* Number of CUDA kernels this library has launched in this process (all meshes and
- * threads), for launch accounting by callers. */
+ * threads), for launch accounting by callers; kernels replayed from the library's CUDA
+ * graphs count once per replay. */
 int64_t chns_kernel_launches(void);
 
 /* Message of the last error on this thread ("" if none). */
