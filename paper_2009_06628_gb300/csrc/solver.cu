@@ -202,13 +202,6 @@ __global__ void to64_kernel(const float* __restrict__ a, double* __restrict__ b,
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         b[i] = (double)a[i];
 }
-// y = alpha * x (alpha read from device scalar sc[idx], optionally inverted)
-__global__ void scale_kernel(const double* __restrict__ x, double* __restrict__ y, int64_t n,
-                             const double* __restrict__ sc, int idx, double mult, int invert) {
-    const double s = invert ? mult / sc[idx] : mult * sc[idx];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = s * x[i];
-}
 // w -= sum_{j<k} h[j] V_j  (h in device memory)
 __global__ void gs_update_kernel(const double* __restrict__ V, int64_t ld, int k, const double* __restrict__ h,
                                  double* __restrict__ w, int64_t n) {
@@ -663,10 +656,6 @@ __global__ void mu_kernel(DevMesh m, double Cn2, const double* __restrict__ U, c
     }
 }
 
-__global__ void extract_mu_kernel(const double* __restrict__ U, int NF, int f, int64_t N, double* __restrict__ out) {
-    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n < N) out[n] = U[(size_t)n * NF + f];
-}
 __global__ void insert_mu_kernel(const double* __restrict__ in, int NF, int f, int64_t N, double* __restrict__ U) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n < N) U[(size_t)n * NF + f] = in[n];
@@ -877,23 +866,9 @@ __global__ void schur_matvec_kernel(DevMesh m, const float* __restrict__ ce, con
     }
 }
 
-__global__ void dotf_kernel(const float* __restrict__ a, const float* __restrict__ b, int64_t n, double* partials) {
-    double acc[1] = {0.0};
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        acc[0] += (double)a[i] * (double)b[i];
-    block_reduce_store<1>(acc, partials);
-}
 __global__ void axpbyf_kernel(float a, float* __restrict__ x, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) x[i] *= a;
-}
-__global__ void fill_hash_kernel(float* __restrict__ x, int64_t n) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) {
-        uint32_t h = (uint32_t)i * 2654435761u;
-        h ^= h >> 15;
-        x[i] = (float)(h & 0xffff) / 65536.0f - 0.5f;
-    }
 }
 __constant__ float c_Mref[64];   // Q1 consistent mass of the unit element (2-point Gauss)
 
@@ -1036,11 +1011,6 @@ __global__ void cheb_final_kernel(int64_t N, int NF, int f, const float* __restr
     if (n < N) z[(size_t)n * NF + f] = (TO)(x[n] + d[n]);
 }
 
-// y = dinv .* (K_c x): one power-iteration step
-__global__ void scale_by_kernel(const float* __restrict__ dinv, float* __restrict__ y, int64_t n) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] *= dinv[i];
-}
 
 }  // namespace
 
