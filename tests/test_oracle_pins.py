@@ -328,3 +328,57 @@ def test_mirror_symmetry():
     R = o.residual(prm, U, Un)
     Rm = o.residual(prm, mir(U), mir(Un))
     assert float((Rm - mir(R)).abs().max()) < 1e-11 * float(R.abs().max())
+
+
+@pytest.mark.parametrize("dim,level", [(2, 3), (3, 2)])
+def test_stabilisation_parameters_spot_values(dim, level):
+    """Hand-evaluated tau_m and tau_phi (Definition 2 stabilisation parameters, G = (4/h^2) I
+    on an axis-aligned cube) through the rows of a boundary node, for a state that is
+    constant in space: v~ = v0 + a/2, phi jumps by b, mu = psi'(c), no gravity.  Then
+    R_m = rho~ a / dt, R_c = 0 and R_phi = b / dt are constants, and for a node on the face
+    x_0 = 0 (away from edges) the only surviving integral of a test gradient is
+    int d_0 N_a = -h^(d-1):
+      pressure row  = -(tau_m / rho~) rho~ a_0 / dt * h^(d-1)
+      phi row       = -h^(d-1) (-v~_0 phi~ + tau_m a_0 phi~ / dt + v~_0 tau_phi b / dt) + (b / dt) h^d / 2.
+    The velocity rows of that node are Dirichlet rows; the pressure and phi rows are not.
+    (tau_c multiplies R_c = div v~ = 0 here and is not pinned by this state.)"""
+    leaves = synth.uniform_leaves(dim, level)
+    m = Mesh(dim, level, leaves)
+    o = Oracle(m)
+    cfg = synth.config_params("drop3d" if dim == 3 else "drop2d")
+    cfg.update(Fr=0.0, rho_ratio=4.0, eta_ratio=3.0)
+    prm = Params(**cfg)
+    h = 1.0 / (1 << level)
+    v0 = np.array([0.3, -0.2, 0.1][:dim])
+    a = np.array([0.05, 0.02, -0.01][:dim])
+    c, b = 0.4, 0.02
+    U = np.zeros((m.N, dim + 3))
+    U[:, :dim] = v0
+    U[:, dim + 1] = c
+    U[:, dim + 2] = c ** 3 - c
+    Un = U.copy()
+    Un[:, :dim] = v0 + a
+    Un[:, dim + 1] = c + b
+    Un[:, dim + 2] = U[:, dim + 2]
+    R = o.residual(prm, torch.tensor(U), torch.tensor(Un)).numpy()
+    # the node at x_0 = 0, every other coordinate at the middle of the domain
+    target = np.array([0.0] + [0.5] * (dim - 1))
+    node = int(np.argmin(np.abs(m.x - target).sum(axis=1)))
+    assert np.abs(m.x[node] - target).max() < 1e-12
+    vt = v0 + a / 2
+    pt = c + b / 2
+    rho = 0.5 * (1 + pt) * 1.0 + 0.5 * (1 - pt) / cfg["rho_ratio"]
+    eta = 0.5 * (1 + pt) * 1.0 + 0.5 * (1 - pt) / cfg["eta_ratio"]
+    dt = cfg["dt"]
+    vGv = 4.0 / h ** 2 * float(vt @ vt)
+    GG = 16.0 * dim / h ** 4
+    tau_m = (4.0 / dt ** 2 + vGv + cfg["C_I"] * (eta / (rho * cfg["Re"])) ** 2 * GG) ** -0.5
+    tau_phi = (4.0 / dt ** 2 + vGv + cfg["C_phi"] * (1.0 / (cfg["Pe"] * cfg["Cn"])) ** 2 * GG) ** -0.5
+    face = h ** (dim - 1)
+    p_row = -tau_m * a[0] / dt * face
+    phi_row = -face * (-vt[0] * pt + tau_m * a[0] * pt / dt + vt[0] * tau_phi * b / dt) + (b / dt) * h ** dim / 2
+    assert abs(R[node, dim] - p_row) <= 1e-12 * abs(p_row)
+    assert abs(R[node, dim + 1] - phi_row) <= 1e-12 * abs(phi_row)
+    # potential row: psi' at the mid-point average, -(q, mu~) + (q, psi'(phi~)), int N_a = h^d / 2
+    mu_row = (pt ** 3 - pt - (c ** 3 - c)) * h ** dim / 2
+    assert abs(R[node, dim + 2] - mu_row) <= 1e-12 * abs(mu_row)
