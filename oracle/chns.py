@@ -41,6 +41,13 @@ Readings of the paper taken here (each also listed in the design notes):
     vector) and Newton keeps int p^{k+1} = int p^k by removing the mean of each
     pressure update.
   * No subscale time derivative (quasi-static subscales, as in Definition 2).
+
+Pins (tests/test_oracle_pins.py) fix the Galerkin terms (manufactured solution),
+the invariants (mass row-sum, pressure row-sum, hydrostatic zero), tau_m, tau_phi
+and the stabilisation terms of the pressure and phi rows (hand-evaluated spot
+values).  Parity unpinned (partial): the subgrid momentum terms and tau_c of
+``residual`` rest on the reading of Definition 2 above and are checked only for
+self-consistency (finite differences, adjoint identity).
 """
 import math
 
