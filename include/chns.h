@@ -162,8 +162,12 @@ chns_status chns_vjp(const chns_mesh* mesh, const chns_params* params, const dou
 
 /* One implicit time step (Section 3.4): solve R(U_old, U) = 0 by inexact Newton from
  * U^{0} = U_old (U_inout is overwritten with U_old first) with matrix-free GMRES.
- * U_old, U_inout: device, N * n_f doubles.  stats: host, may be NULL.  Synchronises
- * the stream.  The first call on a mesh allocates the Krylov workspace. */
+ * With pin_pressure = 2, GMRES runs on J + u m_p^T / |Omega| (u = |diag J| on the
+ * pressure rows, m_p the nodal masses): nonsingular, with the zero-mean-pressure
+ * solution of J dU = -R.  U_old, U_inout: device, N * n_f doubles.  stats: host, may
+ * be NULL.  Synchronises the stream (it reads scalars every GMRES iteration).  The
+ * first call on a mesh allocates the Krylov workspace; the pressure-Schur apply is
+ * captured into CUDA graphs on a private stream of the mesh and replayed on `stream`. */
 chns_status chns_newton_step(const chns_mesh* mesh, const chns_params* params,
                              const chns_solver_opts* opts, const double* U_old, double* U_inout,
                              chns_stats* stats, void* stream);
