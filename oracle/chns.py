@@ -42,12 +42,14 @@ Readings of the paper taken here (each also listed in the design notes):
     pressure update.
   * No subscale time derivative (quasi-static subscales, as in Definition 2).
 
-Pins (tests/test_oracle_pins.py) fix the Galerkin terms (manufactured solution),
-the invariants (mass row-sum, pressure row-sum, hydrostatic zero), tau_m, tau_phi
-and the stabilisation terms of the pressure and phi rows (hand-evaluated spot
-values).  Parity unpinned (partial): the subgrid momentum terms and tau_c of
-``residual`` rest on the reading of Definition 2 above and are checked only for
-self-consistency (finite differences, adjoint identity).
+Pins (tests/test_oracle_pins.py, tests/test_oracle_vms_pin.py) fix the Galerkin
+terms (manufactured solution), the invariants (mass row-sum, pressure row-sum,
+hydrostatic zero), tau_m, tau_phi and the stabilisation terms of the pressure and phi
+rows (hand-evaluated spot values), and every term of Definition 2 -- the subgrid
+momentum terms and tau_c included -- at an interior node, against a term-by-term
+sympy evaluation of the printed weak form for a Q1 state in which every term is
+non-zero.  The derivatives (jvp, vjp, jacobian) are pinned by central finite
+differences and the adjoint identity; mass, energy and initial_mu by closed forms.
 """
 import math
 
