@@ -35,14 +35,15 @@ WORKLOAD = ("3D CHNS drop, uniform octree level 6 (64^3 Q1 hexes, 274,625 nodes 
             "rho/eta ratios 10, Re=100 We=10 Pe=100 Fr=1 Cn=0.02 dt=5e-4; one mixed-precision "
             "Newton step to rel. residual 1e-9 per step")
 METRIC = "CHNS J·x GDOF/s & % HBM roofline; mixed vs FP64 Newton step time at ≤1e-9 rel"
-# Executed FP32 floating-point operations of one J x element (ncu: 2 x FFMA + FADD + FMUL
-# thread instructions of the FP32 J x kernel divided by the element count).
-FLOPS_PER_ELEMENT_JVP32 = 14770
-# DRAM bytes per FP32 J x launch on the 64^3 mesh: ncu dram__bytes_read + write of the
-# 128^3 capture (318.57 MB, 2,097,152 elements) scaled by elements (traffic grows with them).
-JVP32_TRAFFIC_BYTES_64 = 318.57e6 * 262144 / 2097152
-# Derived FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Per-element counts of the element kernels taken by ncu from one launch on the 64^3 mesh
+# (profiles/element_kernels_64cubed_counts.md): executed floating-point operations (2 x FMA
+# + ADD + MUL thread instructions of the kernel's precision, divided by the element count)
+# and DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch.  They belong to
+# the kernel sources whose SHA-256 is KERNEL_SRC_SHA; when the sources change, the bench
+# reports them as null (stale) until they are captured again.
+KERNEL_SRC_FILES = ("paper_2009_06628_gb300/csrc/element_kernels.cu", "paper_2009_06628_gb300/csrc/pointwise.cuh")
+KERNEL_SRC_SHA = None
+KERNEL_COUNTS = {}
 
 
 def peaks():
@@ -51,6 +52,22 @@ def peaks():
             return json.load(f)
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
+
+
+def kernel_src_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SRC_FILES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def counts_for(name):
+    """ncu counts of kernel `name` if they belong to the current sources, else None."""
+    if KERNEL_SRC_SHA is None or kernel_src_sha() != KERNEL_SRC_SHA:
+        return None
+    return KERNEL_COUNTS.get(name)
 
 
 def workload_state(x):
@@ -102,40 +119,51 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline_oracle(seconds_hint=True):
-    """The oracle's J x (torch forward mode, FP64, host cores) on a bounded sample of the
-    same workload: the level-5 uniform mesh (32^3 hexes, 35,937 nodes x 6 DOF)."""
+def cpu_baseline_oracle():
+    """The oracle's J x (torch forward mode, FP64, host cores) on the bench workload itself
+    (the 64^3 mesh): one full application with all host threads, and one with a single
+    thread over a 1/16 element subset (32 of the 512 element rows of 512), scaled to the
+    whole mesh by its element count (the oracle's cost is per element)."""
     from oracle import Mesh as OMesh, Oracle, Params as OParams
-    level = 5
-    om = OMesh(DIM, level, synth.uniform_leaves(DIM, level))
-    o = Oracle(om)
+    om = OMesh(DIM, LEVEL, synth.uniform_leaves(DIM, LEVEL))
     cfg, U = workload_state(om.x)
     prm = OParams(**cfg)
     Ut = torch.tensor(U)
     Un = Ut + 1e-4 * torch.tensor(synth.random_vectors(U.size, 1, 7)[0]).reshape(U.shape)
     Un[torch.tensor(om.boundary), :DIM] = 0.0
     x = torch.tensor(synth.random_vectors(U.size, 1, 8)[0]).reshape(U.shape)
-    o.jvp(prm, Ut, Un, x)  # warm-up
-    reps, t0 = 0, time.perf_counter()
-    while True:
-        o.jvp(prm, Ut, Un, x)
-        reps += 1
-        if time.perf_counter() - t0 > 10.0 or reps >= 5:
-            break
-    dt = (time.perf_counter() - t0) / reps
     dof = U.size
-    return {"value": dof / dt / 1e9, "unit": "GDOF/s", "cores": torch.get_num_threads(), "kind": "oracle",
-            "sample": f"oracle J x (FP64 torch forward mode) on the level-5 uniform mesh, {dof} DOF, "
-                      f"{reps} applications, {dt:.2f} s each"}
+    threads = torch.get_num_threads()
+    o = Oracle(om)
+    t0 = time.perf_counter()
+    o.jvp(prm, Ut, Un, x)
+    t_all = time.perf_counter() - t0
+    sub = np.arange(om.E // 16)
+    os1 = Oracle(om, elements=sub)
+    torch.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        os1.jvp(prm, Ut, Un, x)
+        t_one = (time.perf_counter() - t0) * om.E / sub.size
+    finally:
+        torch.set_num_threads(threads)
+    return {"value": dof / t_all / 1e9, "unit": "GDOF/s", "cores": threads, "kind": "oracle",
+            "value_1core": dof / t_one / 1e9,
+            "sample": f"oracle J x (FP64 torch forward mode) on the 64^3 bench mesh ({dof} DOF): one application "
+                      f"on {threads} threads ({t_all:.2f} s); one thread over {sub.size} of {om.E} elements "
+                      f"({t_one * sub.size / om.E:.2f} s, scaled to the mesh)"}
 
 
 def run_reference(args, rank, world):
+    """The oracle's J x on the bench workload (the 64^3 mesh), one bounded sample per step:
+    the first 1/8 of the Morton-ordered elements (32,768 of 262,144), all host threads.
+    value = the DOF share of that sample / time (the oracle's cost is per element)."""
     if rank != 0:
         return 0
     from oracle import Mesh as OMesh, Oracle, Params as OParams
-    level = 5
-    om = OMesh(DIM, level, synth.uniform_leaves(DIM, level))
-    o = Oracle(om)
+    om = OMesh(DIM, LEVEL, synth.uniform_leaves(DIM, LEVEL))
+    sub = np.arange(om.E // 8)
+    o = Oracle(om, elements=sub)
     cfg, U = workload_state(om.x)
     prm = OParams(**cfg)
     Ut = torch.tensor(U)
@@ -147,16 +175,72 @@ def run_reference(args, rank, world):
     for _ in range(args.steps):
         o.jvp(prm, Ut, Un, x)
     dt = (time.perf_counter() - t0) / args.steps
-    v = U.size / dt / 1e9
+    v = U.size * (sub.size / om.E) / dt / 1e9
+    sample = (f"oracle J x (FP64 torch forward mode) over {sub.size} of the {om.E} elements of the 64^3 bench mesh "
+              f"per step, {torch.get_num_threads()} host threads")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GDOF/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "level-5 uniform mesh (32^3 hexes), one oracle J x per step"},
+            "config": {"workload": WORKLOAD, "sample": sample},
             "cpu_baseline": {"value": v, "unit": "GDOF/s", "cores": torch.get_num_threads(), "kind": "oracle",
-                             "sample": "oracle J x on the level-5 uniform mesh (35,937 nodes x 6 DOF) per step"},
+                             "sample": sample},
             "e2e": {"value": v, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def kernel_table(chns, gm, prm, U0, pk, fp32_peak, fp64_peak, reps=10):
+    """Each element kernel alone on the bench mesh: CUDA-event time per launch with L2
+    flushed before every launch (a 256 MiB buffer is overwritten), GDOF/s, algorithmic
+    HBM bytes and their fraction of the measured copy bandwidth, and (when the ncu counts
+    match the sources) flop rate against the measured FMA peak and DRAM traffic."""
+    E, N, nf = gm.E, gm.N, DIM + 3
+    dof = N * nf
+    g = torch.Generator(device="cuda").manual_seed(17)
+    Un = U0 + 1e-4 * torch.randn(U0.shape, device="cuda", dtype=torch.float64, generator=g)
+    x = torch.randn(U0.shape, device="cuda", dtype=torch.float64, generator=g)
+    U0f, Unf, xf = U0.float(), Un.float(), x.float()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    idx = E * (8 * 4 + 1)       # e2n + level (the hanging table is empty on the uniform mesh)
+    kernels = {
+        # name: (launch, precision, algorithmic bytes per launch, unit description)
+        "residual_fp64": (lambda: chns.residual(gm, prm, U0, Un), 0, 3 * dof * 8 + idx,
+                          "read U^k, U^{k+1}; write R"),
+        "jvp_fp64": (lambda: chns.jvp(gm, prm, U0, Un, x), 0, 4 * dof * 8 + idx, "read U^k, U^s, x; write y"),
+        "jvp_fp32": (lambda: chns.jvp(gm, prm, U0f, Unf, xf), 1, 4 * dof * 4 + idx, "read U^k, U^s, x; write y"),
+        "vjp_fp64": (lambda: chns.vjp(gm, prm, U0, Un, x), 0, 5 * dof * 8 + idx + N,
+                     "read U^k, U^s, w, node flags; write g_new, g_old"),
+    }
+    out = {}
+    for name, (fn, prec, nbytes, what) in kernels.items():
+        fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(reps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        ms = tot / reps
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        rec = {"ms": ms, "gdof_s": dof / (ms * 1e-3) / 1e9, "algorithmic_bytes": nbytes, "bytes_read_written": what,
+               "achieved_gbs": gbs, "hbm_frac": gbs / pk.get("hbm_gbs", 6800.0)}
+        cnt = counts_for(name)
+        peak = fp32_peak if prec == 1 else fp64_peak
+        if cnt:
+            tf = cnt["flop_per_element"] * E / (ms * 1e-3) / 1e12
+            rec.update({"flop_per_element": cnt["flop_per_element"], "achieved_tflops": tf,
+                        "peak_tflops": peak, "alu_frac": tf / peak,
+                        "dram_bytes_per_launch": cnt.get("dram_bytes")})
+        else:
+            rec.update({"flop_per_element": None, "achieved_tflops": None, "peak_tflops": peak, "alu_frac": None,
+                        "dram_bytes_per_launch": None})
+        out[name] = rec
+    del flush
+    return out
 
 
 def aggregate_replicas(t_ms, work, dist=None, device="cpu"):
@@ -323,6 +407,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-kernels", action="store_true", help="skip the per-kernel table")
     ap.add_argument("--profile", choices=["jvp32", "jvp64", "residual", "vjp"],
                     help="run only this kernel --reps times on a uniform mesh of --level (for ncu)")
     ap.add_argument("--level", type=int, default=LEVEL)
@@ -365,12 +450,15 @@ def main():
     opts = chns.SolverOpts.make(rtol=1e-9, atol=1e-14, krylov_rtol=1e-3, precision=1, restart=30, max_krylov=2000,
                                 pc_type=1, pc_degree=16)
     U1 = torch.empty_like(U0)
+    # clock samples cover the warm-up and the timed region (the sampler starts before both)
+    clocks = ClockSampler(local)
+    fp32_peak = chns.fma_peak(1, 20000) / 1e12
+    fp64_peak = chns.fma_peak(0, 2000) / 1e12
     for _ in range(args.warmup):
         chns.newton_step(gm, prm, opts, U0, U1)
     torch.cuda.synchronize()
 
     # ---- timed region: K mixed Newton steps from the same U^k ----
-    clocks = ClockSampler(local)
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist:
@@ -392,6 +480,7 @@ def main():
         dist.barrier()
     launches = chns.kernel_launches() - launches0
     clk = clocks.stop()
+    mass_drift = chns.mass(gm, U1) - chns.mass(gm, U0)
     t_ms, total_jvp = aggregate_replicas(ev0.elapsed_time(ev1), float(jvp_calls), dist, dev)
     value = dof * total_jvp / (t_ms * 1e-3) / 1e9
 
@@ -414,7 +503,7 @@ def main():
     e2e_value = dof * e2e_jvp * world / (e2e_ms * 1e-3) / 1e9
 
     # ---- FP64 Newton step on the same problem, and the mixed step's error against it ----
-    newton = {"mixed_ms": t_ms / args.steps, "mixed_stats": stats[-1]}
+    newton = {"mixed_ms": t_ms / args.steps, "mixed_stats": stats[-1], "mixed_mass_drift": mass_drift}
     if not args.no_fp64:
         o64 = chns.SolverOpts.make(rtol=1e-9, atol=1e-14, krylov_rtol=1e-3, precision=0, restart=30, max_krylov=2000,
                                    pc_type=1, pc_degree=16)
@@ -425,20 +514,23 @@ def main():
         f1.record(stream)
         torch.cuda.synchronize()
         newton.update({"fp64_ms": f0.elapsed_time(f1), "fp64_stats": s64.as_dict(),
+                       "fp64_mass_drift": chns.mass(gm, U64) - chns.mass(gm, U0),
                        "rel_err_mixed_vs_fp64": float((U1 - U64).norm() / U64.norm()),
                        "speedup_mixed_vs_fp64": f0.elapsed_time(f1) / (t_ms / args.steps)})
 
     pk = peaks()
+    kernels = kernel_table(chns, gm, prm, U0, pk, fp32_peak, fp64_peak) if not args.no_kernels else None
     E = gm.E
     jvp_avg_ms = jvp_ms / max(jvp_calls, 1)
     hbm_bytes = 4 * dof * 4 + E * (8 * 4 + 1)      # read U^k, U^s, x; write y; e2n + level
-    roof = {"bound": "alu", "unit": "TFLOP/s", "peak": FP32_PEAK_TFLOPS,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
-            "traffic": JVP32_TRAFFIC_BYTES_64 if E == 262144 else None,
-            "flop_per_element": FLOPS_PER_ELEMENT_JVP32}
-    if FLOPS_PER_ELEMENT_JVP32:
-        ach = FLOPS_PER_ELEMENT_JVP32 * E / (jvp_avg_ms * 1e-3) / 1e12
-        roof.update({"achieved": ach, "frac": ach / FP32_PEAK_TFLOPS})
+    cnt = counts_for("jvp_fp32")
+    roof = {"bound": "alu", "unit": "TFLOP/s", "peak": fp32_peak,
+            "peak_source": "measured in this run: chns_fma_peak FP32 (FFMA chains on all SMs, CUDA events)",
+            "traffic": cnt.get("dram_bytes") if cnt else None,
+            "flop_per_element": cnt["flop_per_element"] if cnt else None}
+    if cnt:
+        ach = cnt["flop_per_element"] * E / (jvp_avg_ms * 1e-3) / 1e12
+        roof.update({"achieved": ach, "frac": ach / fp32_peak})
     else:
         roof.update({"achieved": None, "frac": None})
     hbm = {"algorithmic_bytes_per_launch": hbm_bytes, "achieved_gbs": hbm_bytes / (jvp_avg_ms * 1e-3) / 1e9,
@@ -452,6 +544,8 @@ def main():
                        "l2": "inputs larger than L2 (GMRES basis 31 x 13.2 MB FP64, J x operands 26 MB, per step)"},
             "jvp_kernel": {"avg_ms": jvp_avg_ms, "launches": jvp_calls, "gdof_s": dof / (jvp_avg_ms * 1e-3) / 1e9},
             "roofline": roof, "hbm": hbm, "newton": newton, "clocks": clk, "gpu_launches": launches,
+            "alu_peaks_tflops": {"fp32": fp32_peak, "fp64": fp64_peak, "source": "chns_fma_peak, this run"},
+            "kernels": kernels,
             "e2e": {"value": e2e_value, "unit": "GDOF/s", "h2d_bytes_per_step": dof * 8,
                     "d2h_bytes_per_step": dof * 8}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -224,13 +224,25 @@ chns_status chns_mass_solve(const chns_mesh* mesh, const double* rhs, double* x,
  * allowed.  The paper has no counterpart; it is a deployment variant of chns_mass.
  * It allocates nothing: its reduction scratch is a file-scope device array of 16,384
  * doubles (128 KiB, held by every GPU that loads the library until the process exits),
- * so meshes of more than 67,108,864 elements are rejected with CHNS_EINVAL.  U: device,
+ * so meshes of more than 67,108,864 elements are rejected with CHNS_EINVAL, and so is a
+ * call made while another device than the mesh's (the one current at chns_mesh_create)
+ * is current, because the scratch address is the current device's.  U: device,
  * N * n_f doubles; out: one device double, written asynchronously on `stream` (no
  * host synchronisation).  The first call on a device resolves the scratch address for
  * that device (cudaGetSymbolAddress), so make it before any stream capture.  All calls
  * share the one scratch array: calls that overlap on the GPU (other streams, other
  * threads) race and must be serialised by the caller. */
 chns_status chns_mass_static(const chns_mesh* mesh, const double* U, double* out, void* stream);
+
+/* Measured CUDA-core FMA throughput of the current device, the ALU roofline of the
+ * element kernels (a measurement aid; the paper has no counterpart): precision 1 = FP32
+ * FFMA, 0 = FP64 DFMA.  Runs 8 independent fma chains per thread, 16-fold unrolled,
+ * `iters` times, on 4 blocks of 256 threads per SM, once untimed and once between two CUDA
+ * events on `stream`; *flops_per_s (host) = 2 flops per FMA / elapsed time.  scratch:
+ * device buffer of at least 4 * SMs * 256 * (8 for FP64, 4 for FP32) bytes (receives the
+ * chains' sums); CHNS_EINVAL if it is smaller.  Synchronises the stream. */
+chns_status chns_fma_peak(int32_t precision, int32_t iters, void* scratch, int64_t scratch_bytes,
+                          double* flops_per_s, void* stream);
 
 /* Number of CUDA kernels this library has launched in this process (all meshes and
  * threads), for launch accounting by callers; kernels replayed from the library's CUDA

@@ -92,6 +92,7 @@ SIGNATURES = [
     ("chns_free_energy_grad", ctypes.c_int, [P, P, P, P, P, P]),
     ("chns_mu_rhs_vjp", ctypes.c_int, [P, P, P, P, P, P, P]),
     ("chns_mass_solve", ctypes.c_int, [P, P, P, P]),
+    ("chns_fma_peak", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int64, P, P]),
     ("chns_kernel_launches", ctypes.c_int64, []),
     ("chns_last_error", ctypes.c_char_p, []),
 ]
@@ -271,3 +272,14 @@ def initial_mu(mesh, prm, U):
     """Overwrite the mu field of U (in place) with the discrete mu^0 of its phi."""
     _check(load().chns_initial_mu(mesh.handle, ctypes.byref(prm), _ptr(U), _stream()))
     return U
+
+
+def fma_peak(precision=1, iters=20000):
+    """Measured CUDA-core FMA throughput of the current GPU in flop/s (precision 1: FP32,
+    0: FP64), timed with CUDA events on the current stream."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    scratch = torch.empty(4 * sms * 256, dtype=torch.float64, device="cuda")
+    out = ctypes.c_double(0.0)
+    _check(load().chns_fma_peak(precision, iters, ctypes.c_void_p(scratch.data_ptr()), scratch.numel() * 8,
+                                ctypes.byref(out), _stream()))
+    return out.value

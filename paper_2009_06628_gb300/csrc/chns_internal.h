@@ -28,6 +28,7 @@ struct SolverWS;  // Newton-Krylov workspace (solver.cu)
 struct chns_mesh {
     DevMesh dm;
     int32_t max_level;
+    int32_t device = 0;                // CUDA device ordinal that holds the mesh's arrays
     std::vector<int32_t> node_coords;  // host copy, N * dim
     // owning device pointers
     int32_t* d_e2n = nullptr;

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <string>
 
 #include "chns_internal.h"
 #include "reduce.cuh"
@@ -123,6 +124,16 @@ extern "C" chns_status chns_mass_static(const chns_mesh* m, const double* U, dou
     if (m->dm.E > MS_MAX_ELEMENTS) {
         chns_set_error("chns_mass_static: the mesh has more than 67,108,864 elements (the static scratch "
                        "holds 16,384 block sums of 4,096 elements); use chns_mass");
+        return CHNS_EINVAL;
+    }
+    // the scratch address is resolved for the current device, and the kernels read the
+    // mesh's arrays: both must be on the same GPU
+    int dev = 0;
+    cudaError_t de = cudaGetDevice(&dev);
+    if (de != cudaSuccess) return chns_cuda_status(de, "cudaGetDevice");
+    if (dev != m->device) {
+        chns_set_error("chns_mass_static: the mesh was created on device " + std::to_string(m->device) +
+                       " but device " + std::to_string(dev) + " is current; make the mesh's device current");
         return CHNS_EINVAL;
     }
     double* scratch = nullptr;

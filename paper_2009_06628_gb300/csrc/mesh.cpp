@@ -280,6 +280,13 @@ extern "C" chns_status chns_mesh_create(int32_t dim, int32_t max_level, int64_t 
     std::vector<int8_t> level8(E);
     for (int64_t e = 0; e < E; ++e) level8[e] = (int8_t)lv.level[e];
 
+    {
+        cudaError_t de = cudaGetDevice(&m->device);
+        if (de != cudaSuccess) {
+            chns_mesh_destroy(m);
+            return chns_cuda_status(de, "cudaGetDevice");
+        }
+    }
     chns_status st;
     if ((st = dev_upload(&m->d_e2n, e2n)) != CHNS_OK ||
         (st = dev_upload(&m->d_hang, hang)) != CHNS_OK ||

@@ -6,9 +6,11 @@
 // dots, norms, the residual and the update stay FP64 on the device.  With the pressure
 // level set by its mean (pin mode 2) J is singular (constant pressure); GMRES runs on
 // J + u m_p^T / |Omega| instead, which is nonsingular and has the zero-mean solution of
-// J dU = -R.  The
-// Hessenberg least-squares problem is solved on the host (one scalar read-back per
-// Krylov iteration).  Also: the consistent initial chemical potential by CG.
+// J dU = -R.  Gram-Schmidt (including the decision to re-orthogonalise) and the next
+// Arnoldi vector stay on the device; the Hessenberg column goes to the host for the
+// Givens update, and that read-back overlaps the next vector's operator application,
+// which is queued before the host waits.  Also: the consistent initial chemical
+// potential by CG.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -45,7 +47,8 @@ struct SolverWS {
     double* Pinv64 = nullptr;
     double* sc = nullptr;    // device scalars
     double* hsc = nullptr;   // pinned host scalars
-    cudaEvent_t ev[8] = {};   // J x, preconditioner build / apply and Gram-Schmidt timing
+    cudaEvent_t ev[16] = {};  // J x, preconditioner build / apply and Gram-Schmidt timing (two sets
+                              // of J x / apply events alternate between Arnoldi steps)
     // pressure Schur-complement approximation (FP32)
     float* ce = nullptr;     // E element coefficients
     float* kdinv = nullptr;  // N inverse diagonal
@@ -217,7 +220,8 @@ __global__ void gs_update_kernel(const double* __restrict__ V, int64_t ld, int k
 // remaining values to the partner lane): 9 FP64 shuffle-adds per warp instead of 40,
 // which matters because every FP64 add runs on the narrow FP64 pipe.
 __global__ void orth_dots_kernel(const double* __restrict__ V, int64_t ld, int k, const double* __restrict__ w,
-                                 int64_t n, double* __restrict__ partials) {
+                                 int64_t n, double* __restrict__ partials, const double* __restrict__ pred) {
+    if (pred && pred[0] == 0.0) return;   // second pass not needed (decided on the device)
     const int chunk = blockIdx.y;
     const int j0 = chunk * 8;
     const int kk = min(8, k - j0);
@@ -277,7 +281,8 @@ __global__ void orth_dots_kernel(const double* __restrict__ V, int64_t ld, int k
 }
 // out[j] = sum over row blocks (one block per chunk, one warp per value), out_norm = w.w
 __global__ void orth_dots_final_kernel(const double* __restrict__ partials, int nbx, int k, double* __restrict__ out,
-                                       double* __restrict__ out_norm) {
+                                       double* __restrict__ out_norm, const double* __restrict__ pred) {
+    if (pred && pred[0] == 0.0) return;
     const int chunk = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;   // 9 warps
     const int j = warp;
@@ -295,13 +300,63 @@ __global__ void orth_dots_final_kernel(const double* __restrict__ partials, int 
 }
 // w -= sum_{j<k} h[j] V_j, and per-block partials of the new w . w
 __global__ void gs_update_norm_kernel(const double* __restrict__ V, int64_t ld, int k, const double* __restrict__ h,
-                                      double* __restrict__ w, int64_t n, double* __restrict__ partials) {
+                                      double* __restrict__ w, int64_t n, double* __restrict__ partials,
+                                      const double* __restrict__ pred) {
+    if (pred && pred[0] == 0.0) return;
     double acc[1] = {0.0};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double s = w[i];
         for (int j = 0; j < k; ++j) s -= h[j] * V[(size_t)j * ld + i];
         w[i] = s;
         acc[0] += s * s;
+    }
+    block_reduce_store<1>(acc, partials);
+}
+// Second Gram-Schmidt pass only on severe cancellation (|w'|^2 < 0.01 |w|^2 after the
+// first pass; on GB300 every pass is bound by the FP64 pipe): the flag goes to sc[605]
+// for the predicated second-pass kernels; when the pass is skipped its coefficients
+// sc[256..256+k) are zeroed and the norm sc[601] is carried to sc[603], so the host
+// always reads h = h1 + h2 and the final |w|^2 from the same slots.
+__global__ void reorth_decide_kernel(double* __restrict__ sc, int k) {
+    const bool again = sc[601] < 0.01 * sc[600];
+    if (!again)
+        for (int i = threadIdx.x; i < k; i += blockDim.x) sc[256 + i] = 0.0;
+    if (threadIdx.x == 0) {
+        sc[605] = again ? 1.0 : 0.0;
+        if (!again) sc[603] = sc[601];
+    }
+}
+// final_reduce_kernel for one component (same fixed order), skipped when pred[0] == 0
+__global__ void final_reduce1_pred_kernel(const double* __restrict__ partials, int nblocks, double* __restrict__ out,
+                                          const double* __restrict__ pred) {
+    if (pred && pred[0] == 0.0) return;
+    __shared__ double sh[256];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) v += partials[i];
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sh[0];
+}
+// next Arnoldi vector v = w / sqrt(nrm[0]) (zero on breakdown, which the host reports)
+__global__ void scale_next_kernel(const double* __restrict__ w, double* __restrict__ v, int64_t n,
+                                  const double* __restrict__ nrm) {
+    const double a = nrm[0] > 0.0 ? 1.0 / sqrt(nrm[0]) : 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = a * w[i];
+}
+// sum_n m_n (a + b - c)[n*NF + f] into per-block partials (the phi-mass change of a
+// Newton update: a = U, b = dU, c = U^k)
+__global__ void field_mass3_kernel(const double* __restrict__ m, const double* __restrict__ a,
+                                   const double* __restrict__ b, const double* __restrict__ c, int NF, int f,
+                                   int64_t N, double* partials) {
+    double acc[1] = {0.0};
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        const size_t i = (size_t)n * NF + f;
+        acc[0] += m[n] * ((a[i] + b[i]) - c[i]);
     }
     block_reduce_store<1>(acc, partials);
 }
@@ -1238,14 +1293,16 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
         return CHNS_OK;
     };
     // one classical Gram-Schmidt pass against V_0..V_{k-1}: h -> hdev[0..k), |w|^2 before
-    // -> nrm_before, |w|^2 after -> nrm_after (all device scalars)
-    auto orth_pass = [&](int k, double* hdev, double* nrm_before, double* nrm_after) -> chns_status {
+    // -> nrm_before, |w|^2 after -> nrm_after (all device scalars); with pred, every kernel
+    // of the pass returns at once when pred[0] == 0
+    auto orth_pass = [&](int k, double* hdev, double* nrm_before, double* nrm_after,
+                         const double* pred) -> chns_status {
         int nbx = c.g < ORTH_MAX_BX ? c.g : ORTH_MAX_BX;
         const int nch = (k + 7) / 8;
-        { orth_dots_kernel<<<dim3(nbx, nch), 256, 0, c.s>>>(ws->V, c.n, k, ws->w, c.n, ws->part); chns_count_launches(1); }
-        { orth_dots_final_kernel<<<nch, 288, 0, c.s>>>(ws->part, nbx, k, hdev, nrm_before); chns_count_launches(1); }
-        { gs_update_norm_kernel<<<nbx, 256, 0, c.s>>>(ws->V, c.n, k, hdev, ws->w, c.n, m->d_partials); chns_count_launches(1); }
-        { final_reduce_kernel<<<1, 256, 0, c.s>>>(m->d_partials, nbx, 1, nrm_after); chns_count_launches(1); }
+        { orth_dots_kernel<<<dim3(nbx, nch), 256, 0, c.s>>>(ws->V, c.n, k, ws->w, c.n, ws->part, pred); chns_count_launches(1); }
+        { orth_dots_final_kernel<<<nch, 288, 0, c.s>>>(ws->part, nbx, k, hdev, nrm_before, pred); chns_count_launches(1); }
+        { gs_update_norm_kernel<<<nbx, 256, 0, c.s>>>(ws->V, c.n, k, hdev, ws->w, c.n, m->d_partials, pred); chns_count_launches(1); }
+        { final_reduce1_pred_kernel<<<1, 256, 0, c.s>>>(m->d_partials, nbx, nrm_after, pred); chns_count_launches(1); }
         CHNS_CUDA(cudaGetLastError());
         return CHNS_OK;
     };
@@ -1331,6 +1388,45 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
         // below a tenth of what the target needs is wasted)
         const double target = std::max(o->atol, o->rtol * r0);
         const double eta = std::max(o->krylov_rtol, std::min(0.5, 0.1 * target / rn));
+        // w = S J M^{-1} S^{-1} V_j (similarity scaling: the eigenvalues are those of J M^{-1});
+        // the J x / apply timing events come from set es (two sets alternate, so the next
+        // vector's application can be queued before this one's events are read)
+        auto apply_op = [&](int j, int es) -> chns_status {
+            const double* Vj = ws->V + (size_t)j * c.n;
+            cudaEvent_t* E = ws->ev + 8 * es;
+            CHNS_CUDA(cudaEventRecord(E[4], c.s));
+            { unscale_kernel<<<c.g, 256, 0, c.s>>>(Vj, ws->Sd, ws->SR, c.n); chns_count_launches(1); }
+            if (mixed) {
+                { pc_apply_kernel<float, float><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv32, ws->SR, ws->z32); chns_count_launches(1); }
+                if (schur && (st = schur_apply_any((const double*)ws->SR, ws->z32)) != CHNS_OK) return st;
+                if (chblk && (st = ch_apply_any((const double*)ws->SR, ws->z32)) != CHNS_OK) return st;
+                if (pin == 2) pmean(ws->z32);
+                CHNS_CUDA(cudaEventRecord(E[5], c.s));
+                CHNS_CUDA(cudaEventRecord(E[0], c.s));
+                CHNS_CUDA(launch_jvp32(m, pc, ws->Uo32, ws->Us32, ws->z32, ws->y32, pin, c.s));
+                CHNS_CUDA(cudaEventRecord(E[1], c.s));
+                if (pin == 2)
+                    { scale_vec_pmean_kernel<float><<<c.g, 256, 0, c.s>>>(ws->y32, ws->S, ws->w, c.n, NF, D, ws->sc + 610, inv_vol); chns_count_launches(1); }
+                else
+                    { scale_vec_kernel<float><<<c.g, 256, 0, c.s>>>(ws->y32, ws->S, ws->w, c.n); chns_count_launches(1); }
+            } else {
+                { pc_apply_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv64, ws->SR, ws->z64); chns_count_launches(1); }
+                if (schur && (st = schur_apply_any((const double*)ws->SR, ws->z64)) != CHNS_OK) return st;
+                if (chblk && (st = ch_apply_any((const double*)ws->SR, ws->z64)) != CHNS_OK) return st;
+                if (pin == 2) pmean(ws->z64);
+                CHNS_CUDA(cudaEventRecord(E[5], c.s));
+                CHNS_CUDA(cudaEventRecord(E[0], c.s));
+                CHNS_CUDA(launch_jvp64(m, pc, U_old, U, ws->z64, ws->t64, pin, c.s));
+                CHNS_CUDA(cudaEventRecord(E[1], c.s));
+                if (pin == 2)
+                    { scale_vec_pmean_kernel<double><<<c.g, 256, 0, c.s>>>(ws->t64, ws->S, ws->w, c.n, NF, D, ws->sc + 610, inv_vol); chns_count_launches(1); }
+                else
+                    { scale_vec_kernel<double><<<c.g, 256, 0, c.s>>>(ws->t64, ws->S, ws->w, c.n); chns_count_launches(1); }
+            }
+            CHNS_CUDA(cudaGetLastError());
+            S.jvp_calls++;
+            return CHNS_OK;
+        };
         while (true) {
             // V0 = r / ||r||
             double beta = rnorm;
@@ -1339,73 +1435,33 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
             gv[0] = beta;
             int j = 0;
             bool done = false;
+            if ((st = apply_op(0, 0)) != CHNS_OK) return st;
             for (; j < mres && kry < o->max_krylov; ++j, ++kry) {
-                double* Vj = ws->V + (size_t)j * c.n;
-                // w = J M^{-1} V_j
-                if (mixed) {
-                    // similarity scaling: the operator is S J M^{-1} S^{-1} (eigenvalues of J M^{-1})
-                    CHNS_CUDA(cudaEventRecord(ws->ev[4], c.s));
-                    { unscale_kernel<<<c.g, 256, 0, c.s>>>(Vj, ws->Sd, ws->SR, c.n); chns_count_launches(1); }
-                    { pc_apply_kernel<float, float><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv32, ws->SR, ws->z32); chns_count_launches(1); }
-                    if (schur && (st = schur_apply_any((const double*)ws->SR, ws->z32)) != CHNS_OK) return st;
-                    if (chblk && (st = ch_apply_any((const double*)ws->SR, ws->z32)) != CHNS_OK) return st;
-                    if (pin == 2) pmean(ws->z32);
-                    CHNS_CUDA(cudaEventRecord(ws->ev[5], c.s));
-                    CHNS_CUDA(cudaEventRecord(ws->ev[0], c.s));
-                    CHNS_CUDA(launch_jvp32(m, pc, ws->Uo32, ws->Us32, ws->z32, ws->y32, pin, c.s));
-                    CHNS_CUDA(cudaEventRecord(ws->ev[1], c.s));
-                    if (pin == 2)
-                        { scale_vec_pmean_kernel<float><<<c.g, 256, 0, c.s>>>(ws->y32, ws->S, ws->w, c.n, NF, D, ws->sc + 610, inv_vol); chns_count_launches(1); }
-                    else
-                        { scale_vec_kernel<float><<<c.g, 256, 0, c.s>>>(ws->y32, ws->S, ws->w, c.n); chns_count_launches(1); }
-                } else {
-                    CHNS_CUDA(cudaEventRecord(ws->ev[4], c.s));
-                    { unscale_kernel<<<c.g, 256, 0, c.s>>>(Vj, ws->Sd, ws->SR, c.n); chns_count_launches(1); }
-                    { pc_apply_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv64, ws->SR, ws->z64); chns_count_launches(1); }
-                    if (schur && (st = schur_apply_any((const double*)ws->SR, ws->z64)) != CHNS_OK) return st;
-                    if (chblk && (st = ch_apply_any((const double*)ws->SR, ws->z64)) != CHNS_OK) return st;
-                    if (pin == 2) pmean(ws->z64);
-                    CHNS_CUDA(cudaEventRecord(ws->ev[5], c.s));
-                    CHNS_CUDA(cudaEventRecord(ws->ev[0], c.s));
-                    CHNS_CUDA(launch_jvp64(m, pc, U_old, U, ws->z64, ws->t64, pin, c.s));
-                    CHNS_CUDA(cudaEventRecord(ws->ev[1], c.s));
-                    if (pin == 2)
-                        { scale_vec_pmean_kernel<double><<<c.g, 256, 0, c.s>>>(ws->t64, ws->S, ws->w, c.n, NF, D, ws->sc + 610, inv_vol); chns_count_launches(1); }
-                    else
-                        { scale_vec_kernel<double><<<c.g, 256, 0, c.s>>>(ws->t64, ws->S, ws->w, c.n); chns_count_launches(1); }
-                }
-                S.jvp_calls++;
-                // classical Gram-Schmidt with selective re-orthogonalisation
-                double hs[2 * 256 + 1];
-                for (int i = 0; i <= j; ++i) hs[256 + i] = 0.0;
+                const int es = j & 1;
+                // classical Gram-Schmidt with selective re-orthogonalisation (decided on the
+                // device) and the next Arnoldi vector, all queued without a host round trip
+                CHNS_CUDA(cudaEventRecord(ws->ev[6], c.s));
+                chns_status so = orth_pass(j + 1, ws->sc, ws->sc + 600, ws->sc + 601, nullptr);
+                if (so != CHNS_OK) return so;
+                { reorth_decide_kernel<<<1, 256, 0, c.s>>>(ws->sc, j + 1); chns_count_launches(1); }
+                so = orth_pass(j + 1, ws->sc + 256, ws->sc + 602, ws->sc + 603, ws->sc + 605);
+                if (so != CHNS_OK) return so;
+                { scale_next_kernel<<<c.g, 256, 0, c.s>>>(ws->w, ws->V + (size_t)(j + 1) * c.n, c.n, ws->sc + 603); chns_count_launches(1); }
+                CHNS_CUDA(cudaEventRecord(ws->ev[7], c.s));
+                CHNS_CUDA(cudaMemcpyAsync(ws->hsc, ws->sc, 606 * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+                CHNS_CUDA(cudaEventRecord(ws->ev[10], c.s));
+                // queue the next vector's operator application before reading the scalars, so
+                // the GPU works on it while the host updates the Hessenberg column; if this
+                // iteration turns out to be the last one, that result is simply not used
+                if (j + 1 < mres && kry + 1 < o->max_krylov)
+                    if ((st = apply_op(j + 1, es ^ 1)) != CHNS_OK) return st;
+                CHNS_CUDA(cudaEventSynchronize(ws->ev[10]));
                 {
-                    CHNS_CUDA(cudaEventRecord(ws->ev[6], c.s));
-                    chns_status so = orth_pass(j + 1, ws->sc, ws->sc + 600, ws->sc + 601);
-                    if (so != CHNS_OK) return so;
-                    CHNS_CUDA(cudaEventRecord(ws->ev[7], c.s));
-                    CHNS_CUDA(cudaMemcpyAsync(ws->hsc, ws->sc, 602 * sizeof(double), cudaMemcpyDeviceToHost, c.s));
-                    CHNS_CUDA(cudaStreamSynchronize(c.s));
-                    for (int i = 0; i <= j; ++i) hs[i] = ws->hsc[i];
-                    double w2 = ws->hsc[600], wn2 = ws->hsc[601];
-                    // second pass only on severe cancellation (|w'| < 0.1 |w|): on GB300 every
-                    // Gram-Schmidt pass is bound by the FP64 pipe (n (j+1) FP64 FMAs)
-                    if (wn2 < 0.01 * w2) {
-                        so = orth_pass(j + 1, ws->sc + 256, ws->sc + 602, ws->sc + 603);
-                        if (so != CHNS_OK) return so;
-                        CHNS_CUDA(cudaEventRecord(ws->ev[7], c.s));
-                        CHNS_CUDA(cudaMemcpyAsync(ws->hsc + 256, ws->sc + 256, 348 * sizeof(double),
-                                                  cudaMemcpyDeviceToHost, c.s));
-                        CHNS_CUDA(cudaStreamSynchronize(c.s));
-                        for (int i = 0; i <= j; ++i) hs[256 + i] = ws->hsc[256 + i];
-                        wn2 = ws->hsc[603];
-                    }
-                    hs[512] = wn2;
-                }
-                {
+                    cudaEvent_t* E = ws->ev + 8 * es;
                     float ms = 0.0f;
-                    CHNS_CUDA(cudaEventElapsedTime(&ms, ws->ev[0], ws->ev[1]));
+                    CHNS_CUDA(cudaEventElapsedTime(&ms, E[0], E[1]));
                     S.jvp_ms += ms;
-                    CHNS_CUDA(cudaEventElapsedTime(&ms, ws->ev[4], ws->ev[5]));
+                    CHNS_CUDA(cudaEventElapsedTime(&ms, E[4], E[5]));
                     S.apply_ms += ms;
                     CHNS_CUDA(cudaEventElapsedTime(&ms, ws->ev[6], ws->ev[7]));
                     S.orth_ms += ms;
@@ -1415,8 +1471,8 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                         pc_pending = false;
                     }
                 }
-                const double hn = std::sqrt(hs[512]);
-                for (int i = 0; i <= j; ++i) H[(size_t)i * mres + j] = hs[i] + hs[256 + i];
+                const double hn = std::sqrt(ws->hsc[603]);
+                for (int i = 0; i <= j; ++i) H[(size_t)i * mres + j] = ws->hsc[i] + ws->hsc[256 + i];
                 H[(size_t)(j + 1) * mres + j] = hn;
                 if (!std::isfinite(hn)) { chns_set_error("non-finite Arnoldi vector"); S.reason = CHNS_EBREAKDOWN; result = CHNS_EBREAKDOWN; break; }
                 // Givens rotations
@@ -1434,8 +1490,6 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                 gv[j + 1] = -sn[j] * gv[j];
                 gv[j] = cs[j] * gv[j];
                 rnorm = std::fabs(gv[j + 1]);
-                if (hn > 0.0)
-                    { axpby_kernel<<<c.g, 256, 0, c.s>>>(1.0 / hn, ws->w, 0.0, ws->V + (size_t)(j + 1) * c.n, c.n); chns_count_launches(1); }
                 if (rnorm <= eta * bnorm_s || hn == 0.0) {
                     ++j;
                     ++kry;
@@ -1504,6 +1558,16 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
             { field_mass_kernel<<<nbk, 256, 0, c.s>>>(m->d_nmass, ws->dU, NF, D, m->dm.N, m->d_partials); chns_count_launches(1); }
             { final_reduce_kernel<<<1, 256, 0, c.s>>>(m->d_partials, nbk, 1, ws->sc + 600); chns_count_launches(1); }
             { field_shift_kernel<<<c.g, 256, 0, c.s>>>(ws->dU, NF, D, m->dm.N, ws->sc + 600, 1.0 / m->volume); chns_count_launches(1); }
+            CHNS_CUDA(cudaGetLastError());
+        }
+        {
+            // keep int phi^{k+1} = int phi^k (Proposition 1, exact for the solution of the
+            // discrete system) for every inexact iterate too: shift the phi update by the
+            // constant that removes the mass change (the nodal masses sum to |Omega|)
+            const int nbk = c.g < 1024 ? c.g : 1024;
+            { field_mass3_kernel<<<nbk, 256, 0, c.s>>>(m->d_nmass, U, ws->dU, U_old, NF, D + 1, m->dm.N, m->d_partials); chns_count_launches(1); }
+            { final_reduce_kernel<<<1, 256, 0, c.s>>>(m->d_partials, nbk, 1, ws->sc + 606); chns_count_launches(1); }
+            { field_shift_kernel<<<c.g, 256, 0, c.s>>>(ws->dU, NF, D + 1, m->dm.N, ws->sc + 606, 1.0 / m->volume); chns_count_launches(1); }
             CHNS_CUDA(cudaGetLastError());
         }
         { axpy_kernel<<<c.g, 256, 0, c.s>>>(1.0, ws->dU, U, c.n); chns_count_launches(1); }

@@ -87,6 +87,19 @@ def case(request, chns):
     return Case(chns, *request.param)
 
 
+def hanging_parent_rows(om):
+    """Independent nodes that are constraint parents of some hanging corner."""
+    return np.unique(om.parents[om.hanging][om.weights[om.hanging] > 0])
+
+
+def max_abs_on_rows(a, b, rows):
+    """max over the given rows of |a - b|, each field scaled by the largest |b| of that field
+    over all rows (a relative-L2 check alone would dilute a few wrong rows)."""
+    a, b = a.cpu().double(), b.double()
+    scale = b.abs().amax(dim=0).clamp_min(1e-300)
+    return float(((a[rows] - b[rows]).abs() / scale).max())
+
+
 def test_node_numbering_bit_exact(case):
     assert case.gm.N == case.om.N
     assert np.array_equal(case.gm.node_coords(), case.om.nodes.astype(np.int32))
@@ -97,6 +110,9 @@ def test_residual_fp64(chns, case):
     R = chns.residual(case.gm, case.prm, case.Ud, case.Und)
     Ro = case.o.residual(case.oprm, case.U, case.Un)
     assert rel(R, Ro) <= TOL64
+    rows = hanging_parent_rows(case.om)
+    if rows.size:
+        assert max_abs_on_rows(R, Ro, rows) <= 1e-11
     # Dirichlet rows are exact copies
     b = case.om.boundary
     d = case.om.dim
@@ -110,6 +126,9 @@ def test_jvp_fp64_many_directions(chns, case):
         y = chns.jvp(case.gm, case.prm, case.Ud, case.Und, x.to(case.dev))
         yo = case.o.jvp(case.oprm, case.U, case.Un, x)
         assert rel(y, yo) <= TOL64, i
+        rows = hanging_parent_rows(case.om)
+        if rows.size:
+            assert max_abs_on_rows(y, yo, rows) <= 1e-11, i
 
 
 def test_jvp_fp32(chns, case):
@@ -119,6 +138,9 @@ def test_jvp_fp32(chns, case):
     yo = case.o.jvp(case.oprm, case.U, case.Un, x)
     assert y.dtype == torch.float32
     assert rel(y.double(), yo) <= TOL32
+    rows = hanging_parent_rows(case.om)
+    if rows.size:
+        assert max_abs_on_rows(y, yo, rows) <= 1e-5
 
 
 def test_vjp_fp64(chns, case):
@@ -127,6 +149,10 @@ def test_vjp_fp64(chns, case):
     gno, goo, gco = case.o.vjp(case.oprm, case.U, case.Un, w)
     assert rel(gn, gno) <= TOL64
     assert rel(go, goo) <= TOL64
+    rows = hanging_parent_rows(case.om)
+    if rows.size:
+        assert max_abs_on_rows(gn, gno, rows) <= 1e-11
+        assert max_abs_on_rows(go, goo, rows) <= 1e-11
     assert abs(float(gc.cpu()[0]) - float(gco)) <= TOL64 * max(1.0, abs(float(gco))) * 10
 
 
@@ -157,3 +183,51 @@ def test_initial_mu(chns, case):
     assert rel(U[:, d + 2], mu_o) <= 1e-11
     # other fields untouched
     assert torch.equal(U[:, : d + 2], case.Und[:, : d + 2])
+
+
+def test_config2_full_vector_parity_64cubed(chns):
+    """The 64^3 workload of the benchmark (uniform octree level 6, 274,625 nodes x 6 DOF, the
+    tanh drop of radius 0.2 with Cn = 0.02, the 8-mode divergence-free velocity, density and
+    viscosity ratios 10, gravity along -z): full-vector parity of the residual, FP64 J x (two
+    directions), FP32 J x and J^T w (with its U^k and Cn parts) with the oracle."""
+    import bench
+    level = 6
+    leaves = synth.uniform_leaves(3, level)
+    om = OMesh(3, level, leaves)
+    gm = chns.Mesh(3, level, leaves)
+    cfg, U = bench.workload_state(om.x)
+    o = Oracle(om)
+    oprm = OParams(**cfg)
+    prm = chns.Params.make(**cfg)
+    U = torch.tensor(U)
+    U[:, 5] = 0.1 * torch.tensor(synth.random_vectors(om.N, 1, 6)[0])
+    Un = U + 1e-4 * torch.tensor(synth.random_vectors(U.numel(), 1, 7)[0]).reshape(U.shape)
+    Un[torch.tensor(om.boundary), :3] = 0.0
+    dev = torch.device("cuda")
+    Ud, Und = U.to(dev), Un.to(dev)
+    assert rel(chns.residual(gm, prm, Ud, Und), o.residual(oprm, U, Un)) <= TOL64
+    X = synth.random_vectors(U.numel(), 2, 501)
+    for i in range(2):
+        x = torch.tensor(X[i]).reshape(U.shape)
+        yo = o.jvp(oprm, U, Un, x)
+        assert rel(chns.jvp(gm, prm, Ud, Und, x.to(dev)), yo) <= TOL64, i
+        if i == 0:
+            f = lambda t: t.to(dev, torch.float32)
+            y32 = chns.jvp(gm, prm, f(U), f(Un), f(x))
+            assert rel(y32.double(), yo) <= TOL32
+    w = torch.tensor(synth.random_vectors(U.numel(), 1, 502)[0]).reshape(U.shape)
+    gn, go, gc = chns.vjp(gm, prm, Ud, Und, w.to(dev))
+    gno, goo, gco = o.vjp(oprm, U, Un, w)
+    assert rel(gn, gno) <= TOL64
+    assert rel(go, goo) <= TOL64
+    assert abs(float(gc.cpu()[0]) - float(gco)) <= 1e-11 * max(1.0, abs(float(gco)))
+
+
+def test_fma_peak_probe(chns):
+    """The measured CUDA-core FMA rates behind the ALU rooflines are in the range the
+    unit counts allow: FP32 at most 152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s
+    (above half of it), FP64 well below FP32."""
+    f32 = chns.fma_peak(1, 20000)
+    f64 = chns.fma_peak(0, 2000)
+    assert 40e12 < f32 < 82e12, f32
+    assert 0.1e12 < f64 < f32 / 8, (f64, f32)

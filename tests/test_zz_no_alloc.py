@@ -49,9 +49,14 @@ def test_mass_static_matches_mass_on_two_calls(chns, dim, kind):
         U[:, dim + 1] = synth.drop_phi(x, [[0.5] * dim], [0.2 + 0.05 * call], 0.02, noise=1e-3, seed=seed)
         Ud = torch.tensor(U, device="cuda")
         expected = chns.mass(gm, Ud)
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         code = lib.chns_mass_static(gm.handle, ctypes.c_void_p(Ud.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                     stream)
         assert code == 0, lib.chns_last_error().decode()
         torch.cuda.synchronize()
+        if call == 1:
+            # the first call may load the library's kernels; the second takes no device memory
+            assert torch.cuda.mem_get_info()[0] == free_before
         got = float(out.cpu()[0])
         assert abs(got - expected) <= TOL * max(1.0, abs(expected)), (call, got, expected)
