@@ -96,8 +96,16 @@ typedef struct {
                             2: as 1, with phi and mu preconditioned together by the
                             Cahn-Hilliard block: mu eliminated with the mass matrix and the
                             phi Schur complement approximated by (1/dt)(M + eps K) M^{-1}
-                            (M + eps K), eps^2 = dt Cn/(2 Pe), two Chebyshev solves (FP32) */
-    int32_t pc_degree;   /* Chebyshev degree for pc_type 1, in [2, 200] */
+                            (M + eps K), eps^2 = dt Cn/(2 Pe), two Chebyshev solves (FP32);
+                            3: as 1, with the pressure Schur Laplacian inverted by one
+                            geometric multigrid V-cycle on the octree's levels (each coarser
+                            level caps the leaves one level shallower; Q1 prolongation, its
+                            transpose as restriction, Jacobi-Chebyshev smoothing of degree
+                            pc_degree, a degree-40 Chebyshev sweep on the coarsest level, FP32);
+                            4: as 3, with the Cahn-Hilliard block of 2.  The hierarchy is built
+                            (host work and device memory held by the mesh) on the first call
+                            that asks for it. */
+    int32_t pc_degree;   /* Chebyshev degree for pc_type 1/2 (whole apply) or 3/4 (smoother), in [2, 200] */
 } chns_solver_opts;
 
 #define CHNS_HIST 32
@@ -233,6 +241,33 @@ chns_status chns_mass_solve(const chns_mesh* mesh, const double* rhs, double* x,
  * share the one scratch array: calls that overlap on the GPU (other streams, other
  * threads) race and must be serialised by the caller. */
 chns_status chns_mass_static(const chns_mesh* mesh, const double* U, double* out, void* stream);
+
+/* Transfer between the Q1 spaces of two meshes of the same domain and dimension (Section 4:
+ * parent-child interpolation on the octree, used for remeshing and by the multigrid
+ * preconditioner).  P maps a field on `src` to the independent nodes of `dst`: each node
+ * of dst takes the value of src's Q1 interpolant (hanging constraints of src included)
+ * at its position, so P is exact when dst refines src and is injection when dst coarsens
+ * src.  Built on the host from the meshes' leaf data; its rows and those of P^T are held
+ * on the current device.  Free with chns_transfer_destroy. */
+typedef struct chns_transfer chns_transfer;
+chns_status chns_transfer_create(const chns_mesh* src, const chns_mesh* dst, chns_transfer** out);
+void chns_transfer_destroy(chns_transfer* t);
+int64_t chns_transfer_nnz(const chns_transfer* t);   /* stored weights of P (-1 for NULL) */
+/* transpose = 0: out (dst nodes x nf) = P in (src nodes x nf); transpose = 1: out (src nodes
+ * x nf) = P^T in (dst nodes x nf).  Node-major interleaved FP64 device vectors, nf in
+ * [1, 16]; out is overwritten; asynchronous on `stream`. */
+chns_status chns_transfer_apply(const chns_transfer* t, int32_t nf, int32_t transpose, const double* in,
+                                double* out, void* stream);
+
+/* Host-only (no device work): the leaf list with every leaf deeper than `cap` replaced by
+ * its ancestor at level `cap` (Morton order kept, duplicates merged), as the multigrid
+ * hierarchy builds its coarse levels.  leaves: n_leaves Morton-sorted leaves with anchors in
+ * units of 2^-max_level; out (host, room for n_leaves): the capped leaves with anchors in
+ * units of 2^-cap; fmap (host, n_leaves, may be NULL): the output leaf of every input leaf;
+ * *n_out: the output count.  A complete 2:1-balanced input gives a complete 2:1-balanced
+ * output. */
+chns_status chns_coarsen_leaves(int32_t dim, int32_t max_level, int64_t n_leaves, const chns_leaf* leaves,
+                                int32_t cap, chns_leaf* out, int32_t* fmap, int64_t* n_out);
 
 /* Measured CUDA-core FMA throughput of the current device, the ALU roofline of the
  * element kernels (a measurement aid; the paper has no counterpart): precision 1 = FP32

@@ -133,3 +133,33 @@ class Mesh:
         self.hanging = hanging.reshape(E, nc)
         # physical corner coordinates (E, nc, d)
         self.corner_x = self.lo + (self.hi - self.lo) * corners.astype(np.float64) / float(n_side)
+
+    def interpolate_at(self, U, points):
+        """Values at physical points (P, d) of the conforming Q1 field with nodal values U
+        (N, ...): the leaf containing each point (the first one found, searched by brute
+        force over all leaves), the point's local coordinates t in [0, 1]^d there, and the
+        Q1 weights prod_k (t_k or 1 - t_k) of the leaf's corners, each corner taken through
+        its hanging-node parents and weights.  A point on a face shared by two leaves gets
+        the same value from either, because the field is continuous."""
+        U = np.asarray(U, dtype=np.float64)
+        pts = np.asarray(points, dtype=np.float64)
+        d = self.dim
+        lo = self.anchors.astype(np.float64) / float(1 << self.max_level)
+        size = self.size.astype(np.float64) / float(1 << self.max_level)
+        lo = self.lo + (self.hi - self.lo) * lo
+        size = (self.hi - self.lo) * size
+        out = np.zeros((pts.shape[0],) + U.shape[1:])
+        for i, p in enumerate(pts):
+            inside = np.all((p[None, :] >= lo - 1e-14) & (p[None, :] <= lo + size[:, None] + 1e-14), axis=1)
+            e = int(np.nonzero(inside)[0][0])
+            t = (p - lo[e]) / size[e]
+            val = np.zeros(U.shape[1:])
+            for a in range(self.nc):
+                w = 1.0
+                for k in range(d):
+                    w *= t[k] if (a >> k) & 1 else 1.0 - t[k]
+                for j in range(4):
+                    if self.weights[e, a, j] > 0:
+                        val = val + w * self.weights[e, a, j] * U[self.parents[e, a, j]]
+            out[i] = val
+        return out

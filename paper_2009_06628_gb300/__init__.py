@@ -92,6 +92,12 @@ SIGNATURES = [
     ("chns_free_energy_grad", ctypes.c_int, [P, P, P, P, P, P]),
     ("chns_mu_rhs_vjp", ctypes.c_int, [P, P, P, P, P, P, P]),
     ("chns_mass_solve", ctypes.c_int, [P, P, P, P]),
+    ("chns_transfer_create", ctypes.c_int, [P, P, ctypes.POINTER(ctypes.c_void_p)]),
+    ("chns_transfer_destroy", None, [P]),
+    ("chns_transfer_nnz", ctypes.c_int64, [P]),
+    ("chns_transfer_apply", ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P, P, P]),
+    ("chns_coarsen_leaves", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, P, ctypes.c_int32, P, P,
+                                           ctypes.POINTER(ctypes.c_int64)]),
     ("chns_fma_peak", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int64, P, P]),
     ("chns_kernel_launches", ctypes.c_int64, []),
     ("chns_last_error", ctypes.c_char_p, []),
@@ -283,3 +289,50 @@ def fma_peak(precision=1, iters=20000):
     _check(load().chns_fma_peak(precision, iters, ctypes.c_void_p(scratch.data_ptr()), scratch.numel() * 8,
                                 ctypes.byref(out), _stream()))
     return out.value
+
+
+class Transfer:
+    """Owns a chns_transfer: Q1 interpolation from mesh `src` to the nodes of mesh `dst`."""
+
+    def __init__(self, src, dst):
+        h = ctypes.c_void_p()
+        _check(load().chns_transfer_create(src.handle, dst.handle, ctypes.byref(h)))
+        self._h = h
+        self.n_src, self.n_dst = src.N, dst.N
+
+    @property
+    def nnz(self):
+        return int(load().chns_transfer_nnz(self._h))
+
+    def apply(self, u, transpose=False):
+        """P u (u: n_src x nf) or P^T u (u: n_dst x nf), FP64 CUDA tensors."""
+        u = u.contiguous()
+        nf = 1 if u.dim() == 1 else u.shape[1]
+        rows = self.n_src if transpose else self.n_dst
+        out = torch.empty((rows,) + tuple(u.shape[1:]), dtype=torch.float64, device=u.device)
+        _check(load().chns_transfer_apply(self._h, nf, 1 if transpose else 0, _ptr(u), _ptr(out), _stream()))
+        return out
+
+    def close(self):
+        if self._h and self._h.value:
+            load().chns_transfer_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def coarsen_leaves(dim, max_level, leaves, cap):
+    """Host-only: (capped leaves (m, 4) int32 with anchors in units of 2^-cap, map (n,) int32)."""
+    import numpy as np
+    lv = np.ascontiguousarray(np.asarray(leaves, dtype=np.int32).reshape(-1, 4))
+    out = np.zeros_like(lv)
+    fmap = np.zeros(lv.shape[0], dtype=np.int32)
+    n = ctypes.c_int64(0)
+    _check(load().chns_coarsen_leaves(dim, max_level, lv.shape[0], lv.ctypes.data_as(ctypes.c_void_p), cap,
+                                      out.ctypes.data_as(ctypes.c_void_p), fmap.ctypes.data_as(ctypes.c_void_p),
+                                      ctypes.byref(n)))
+    return out[:n.value].copy(), fmap

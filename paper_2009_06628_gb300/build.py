@@ -9,7 +9,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libchns.so")
-SOURCES = ["mesh.cpp", "capi.cpp", "element_kernels.cu", "reduce_kernels.cu", "solver.cu", "mass_static.cu", "objective.cu", "peaks.cu"]
+SOURCES = ["mesh.cpp", "capi.cpp", "element_kernels.cu", "reduce_kernels.cu", "solver.cu", "mass_static.cu", "objective.cu", "peaks.cu", "multigrid.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fopenmp",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -39,7 +39,8 @@ def build(verbose=False, extra=()):
             if log.strip():
                 print(log, file=sys.stderr)
     objs = [o for o, _ in results]
-    cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-Xcompiler", "-fopenmp", "-o", LIB] + objs + ["-lgomp"]
+    cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-Xcompiler", "-fopenmp", "-Xlinker", "--no-undefined",
+                             "-o", LIB] + objs + ["-lgomp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

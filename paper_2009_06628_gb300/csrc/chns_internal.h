@@ -24,12 +24,18 @@ struct DevMesh {
 };
 
 struct SolverWS;  // Newton-Krylov workspace (solver.cu)
+struct MGHier;    // geometric multigrid hierarchy of the pressure Schur Laplacian (multigrid.cu)
 
 struct chns_mesh {
     DevMesh dm;
     int32_t max_level;
     int32_t device = 0;                // CUDA device ordinal that holds the mesh's arrays
     std::vector<int32_t> node_coords;  // host copy, N * dim
+    // host copies of the element arrays (transfer operators, coarse meshes, remeshing)
+    std::vector<int32_t> h_e2n;        // E * nc
+    std::vector<int32_t> h_hang;       // max(H, 1) * 4
+    std::vector<int32_t> h_anchor;     // E * dim
+    std::vector<int8_t> h_level;       // E
     // owning device pointers
     int32_t* d_e2n = nullptr;
     int32_t* d_hang = nullptr;
@@ -45,6 +51,7 @@ struct chns_mesh {
     double* h_pinned = nullptr;      // pinned host landing zone for scalar results
     unsigned int* d_flags = nullptr; // bit 0: a tau radicand was not positive
     SolverWS* ws = nullptr;
+    MGHier* mg = nullptr;
 };
 
 // Kernel-side parameter block derived from chns_params (all FP64; kernels cast).
@@ -86,6 +93,64 @@ cudaError_t launch_dot(const chns_mesh* m, const double* a, const double* b, int
                        cudaStream_t s);
 cudaError_t launch_multidot(const chns_mesh* m, const double* V, int64_t ld, int k, const double* w, int64_t n,
                             double* out_dev, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------
+// Transfer between the Q1 spaces of two meshes of the same domain (multigrid.cu):
+// P u = the source field interpolated at the target's independent nodes (Q1 on the
+// source element containing the node, source hanging constraints folded in), stored as
+// CSR rows over target nodes, together with its transpose (rows over source nodes), in
+// FP64 and FP32.  Exact (no loss) when the target mesh refines the source mesh.
+struct TransferDev {
+    int64_t n_src = 0, n_dst = 0, nnz = 0;
+    int64_t* rp = nullptr;   // n_dst + 1
+    int32_t* col = nullptr;  // nnz source nodes
+    double* w = nullptr;
+    float* wf = nullptr;
+    int64_t* rpT = nullptr;  // n_src + 1
+    int32_t* colT = nullptr; // nnz target nodes
+    double* wT = nullptr;
+    float* wTf = nullptr;
+};
+chns_status transfer_build(const chns_mesh* src, const chns_mesh* dst, TransferDev* T);
+void transfer_free(TransferDev* T);
+// out = P in (transpose = false; in: n_src x nf, out: n_dst x nf) or P^T in (transpose = true),
+// FP64, overwriting out
+cudaError_t transfer_apply_f64(const TransferDev& T, bool transpose, int nf, const double* in, double* out,
+                               cudaStream_t s);
+// scalar FP32 fields: out (+)= P in or P^T in
+cudaError_t transfer_apply_f32(const TransferDev& T, bool transpose, bool add, const float* in, float* out,
+                               cudaStream_t s);
+
+// Geometric multigrid hierarchy of the pressure Schur Laplacian (multigrid.cu builds it,
+// solver.cu sets it up and applies V-cycles).  Level 0 is the mesh itself; level l + 1 caps
+// every leaf of level l at (deepest level of l) - 1, which keeps the octree complete and
+// 2:1 balanced and makes its Q1 space a subspace of level l's.
+struct MGLevel {
+    chns_mesh* mesh = nullptr;  // owned coarse mesh (null for level 0)
+    DevMesh dm;                 // the level's mesh as kernels see it
+    int64_t N = 0, E = 0;
+    TransferDev P;              // this level -> level - 1 (level >= 1)
+    int32_t* fmap = nullptr;    // for every element of level - 1: its element on this level
+    float* ce = nullptr;        // element coefficients of the Schur Laplacian
+    float* dinv = nullptr;      // inverse diagonal
+    float* bnd = nullptr;       // absolute-row-sum bounds (Gershgorin)
+    float* b = nullptr;         // right-hand side, solution, residual
+    float* x = nullptr;
+    float* t = nullptr;
+    float* cr = nullptr;        // Chebyshev work vectors
+    float* cx = nullptr;
+    float* cd = nullptr;
+    float* cy = nullptr;
+    std::vector<float> c1, c2;  // Chebyshev recurrence coefficients of this level
+    float inv_theta = 0.0f;
+    int deg = 0;
+};
+struct MGHier {
+    std::vector<MGLevel> lv;
+    unsigned int* kmax = nullptr;   // per-level Gershgorin bounds (float bits)
+};
+chns_status mg_hier_build(chns_mesh* m);   // no-op when m->mg exists
+void chns_mg_free(MGHier* mg);
 
 // launch accounting (capi.cpp)
 void chns_count_launches(int n);

@@ -8,34 +8,9 @@
 #include <new>
 
 #include "chns_internal.h"
+#include "morton.h"
 
 namespace {
-
-inline uint64_t part1by1(uint64_t x) {
-    x &= 0xffffffffull;
-    x = (x | (x << 16)) & 0x0000ffff0000ffffull;
-    x = (x | (x << 8)) & 0x00ff00ff00ff00ffull;
-    x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0full;
-    x = (x | (x << 2)) & 0x3333333333333333ull;
-    x = (x | (x << 1)) & 0x5555555555555555ull;
-    return x;
-}
-
-inline uint64_t part1by2(uint64_t x) {
-    x &= 0x1fffffull;
-    x = (x | (x << 32)) & 0x1f00000000ffffull;
-    x = (x | (x << 16)) & 0x1f0000ff0000ffull;
-    x = (x | (x << 8)) & 0x100f00f00f00f00full;
-    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
-    x = (x | (x << 2)) & 0x1249249249249249ull;
-    return x;
-}
-
-// Morton key, x in bit 0 of each group of `dim` bits.
-inline uint64_t morton(int dim, const int64_t* c) {
-    if (dim == 2) return part1by1((uint64_t)c[0]) | (part1by1((uint64_t)c[1]) << 1);
-    return part1by2((uint64_t)c[0]) | (part1by2((uint64_t)c[1]) << 1) | (part1by2((uint64_t)c[2]) << 2);
-}
 
 struct Leaves {
     int dim, L;
@@ -325,15 +300,21 @@ extern "C" chns_status chns_mesh_create(int32_t dim, int32_t max_level, int64_t 
     dm.lo = lo;
     dm.hi = hi;
     m->volume = (d == 2) ? dom * dom : dom * dom * dom;
+    m->h_e2n = std::move(e2n);
+    m->h_hang = std::move(hang);
+    m->h_anchor = std::move(anchor32);
+    m->h_level = std::move(level8);
     *out = m;
     return CHNS_OK;
 }
 
 void chns_solver_ws_free(SolverWS* ws);  // solver.cu
+void chns_mg_free(MGHier* mg);           // multigrid.cu
 
 extern "C" void chns_mesh_destroy(chns_mesh* m) {
     if (!m) return;
     if (m->ws) chns_solver_ws_free(m->ws);
+    if (m->mg) chns_mg_free(m->mg);
     cudaFree(m->d_e2n);
     cudaFree(m->d_hang);
     cudaFree(m->d_level);

@@ -60,6 +60,7 @@ struct SolverWS {
         void* zout = nullptr;
         size_t to = 0;
         int gen = -1;
+        int nk = 0;   // kernels in the graph (launch accounting)
     } sgraph[4];
     cudaStream_t cap = nullptr;
     int schur_gen = 0;
@@ -893,15 +894,15 @@ __global__ void gershgorin_max_kernel(const float* __restrict__ bnd, const float
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(v));
 }
 
-// y += K_c x  (y zeroed by the caller)
+// y += sgn K_c x  (y zeroed, or holding a right-hand side, by the caller)
 template <int D>
 __global__ void schur_matvec_kernel(DevMesh m, const float* __restrict__ ce, const float* __restrict__ x,
-                                    float* __restrict__ y) {
+                                    float* __restrict__ y, float sgn = 1.0f) {
     constexpr int NC = 1 << D;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= m.E) return;
     const float h = (float)ldexp(m.hi - m.lo, -(int)m.level[e]);
-    const float ch = ce[e] * (D == 2 ? 1.0f : h);
+    const float ch = sgn * ce[e] * (D == 2 ? 1.0f : h);
     int par[NC][4], np[NC];
     schur_corners<D>(m, e, par, np);
     float xl[NC];
@@ -1067,6 +1068,100 @@ __global__ void cheb_final_kernel(int64_t N, int NF, int f, const float* __restr
 }
 
 
+// ---------------- geometric multigrid for the pressure Schur Laplacian ----------------
+// coarse element coefficients: the volume-weighted mean of the fine elements they hold
+__global__ void mg_restrict_ce_kernel(int64_t Ef, int D, const int32_t* __restrict__ fmap,
+                                      const int8_t* __restrict__ lev_f, const int8_t* __restrict__ lev_c,
+                                      const float* __restrict__ ce_f, float* __restrict__ ce_c) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= Ef) return;
+    const int c = fmap[e];
+    atomicAdd(ce_c + c, ldexpf(ce_f[e], -D * ((int)lev_f[e] - (int)lev_c[c])));
+}
+__global__ void mg_copy_kernel(int64_t N, const float* __restrict__ a, float* __restrict__ b) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n < N) b[n] = a[n];
+}
+template <class TI>
+__global__ void mg_load_kernel(int64_t N, int NF, int f, const TI* __restrict__ v, float* __restrict__ b) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n < N) b[n] = (float)v[(size_t)n * NF + f];
+}
+template <class TO>
+__global__ void mg_store_kernel(int64_t N, int NF, int f, const float* __restrict__ x, TO* __restrict__ z) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n < N) z[(size_t)n * NF + f] = (TO)x[n];
+}
+// out += x + d (a Chebyshev correction added to an existing iterate)
+__global__ void cheb_final_add_kernel(int64_t N, const float* __restrict__ x, const float* __restrict__ d,
+                                      float* __restrict__ out) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n < N) out[n] += x[n] + d[n];
+}
+
+// Chebyshev coefficients of the three-term recurrence on [alpha, beta] (degree deg)
+void cheb_coeffs(double alpha, double beta, int deg, std::vector<float>& c1, std::vector<float>& c2, float& inv_theta) {
+    const double theta = 0.5 * (beta + alpha), delta = 0.5 * (beta - alpha), sigma = theta / delta;
+    c1.assign(std::max(deg, 1), 0.0f);
+    c2.assign(std::max(deg, 1), 0.0f);
+    double rho = 1.0 / sigma;
+    for (int k = 0; k + 1 < deg; ++k) {
+        const double rn = 1.0 / (2.0 * sigma - rho);
+        c1[k] = (float)(rn * rho);
+        c2[k] = (float)(2.0 * rn / delta);
+        rho = rn;
+    }
+    inv_theta = (float)(1.0 / theta);
+}
+
+// One V-cycle for K x = b on level l (x overwritten), queued on stream st; returns the
+// number of kernels queued.  Each level: Chebyshev pre-smoothing from x = 0, residual,
+// restriction P^T, the coarser cycle, prolongation P added to x, residual, Chebyshev
+// post-smoothing added to x; the coarsest level is one long Chebyshev sweep.
+int mg_vcycle(MGHier* mg, int l, const float* ce0, cudaStream_t st) {
+    MGLevel& L = mg->lv[(size_t)l];
+    const float* ce = l == 0 ? ce0 : L.ce;
+    const int D = L.dm.dim;
+    const int gN = (int)((L.N + 255) / 256), gE = (int)((L.E + 255) / 256);
+    int nk = 0;
+    auto matvec = [&](const float* x, float* y, float sgn) {
+        if (D == 2) schur_matvec_kernel<2><<<gE, 256, 0, st>>>(L.dm, ce, x, y, sgn);
+        else schur_matvec_kernel<3><<<gE, 256, 0, st>>>(L.dm, ce, x, y, sgn);
+        ++nk;
+    };
+    auto cheb = [&](const float* in, float* out, bool add) {
+        cheb_init_kernel<float><<<gN, 256, 0, st>>>(L.N, 1, 0, in, L.dinv, L.cr, L.cx, L.cd, L.cy, L.inv_theta);
+        ++nk;
+        for (int k = 0; k + 1 < L.deg; ++k) {
+            matvec(L.cd, L.cy, 1.0f);
+            cheb_step_kernel<<<gN, 256, 0, st>>>(L.N, L.dinv, L.cr, L.cx, L.cd, L.cy, L.c1[(size_t)k], L.c2[(size_t)k]);
+            ++nk;
+        }
+        if (add) cheb_final_add_kernel<<<gN, 256, 0, st>>>(L.N, L.cx, L.cd, out);
+        else cheb_final_kernel<float><<<gN, 256, 0, st>>>(L.N, 1, 0, L.cx, L.cd, out);
+        ++nk;
+    };
+    if (l + 1 == (int)mg->lv.size()) {
+        cheb(L.b, L.x, false);
+        return nk;
+    }
+    MGLevel& C = mg->lv[(size_t)l + 1];
+    cheb(L.b, L.x, false);
+    mg_copy_kernel<<<gN, 256, 0, st>>>(L.N, L.b, L.t);
+    ++nk;
+    matvec(L.x, L.t, -1.0f);
+    transfer_apply_f32(C.P, true, false, L.t, C.b, st);
+    ++nk;
+    nk += mg_vcycle(mg, l + 1, ce0, st);
+    transfer_apply_f32(C.P, false, true, C.x, L.x, st);
+    ++nk;
+    mg_copy_kernel<<<gN, 256, 0, st>>>(L.N, L.b, L.t);
+    ++nk;
+    matvec(L.x, L.t, -1.0f);
+    cheb(L.t, L.x, true);
+    return nk;
+}
+
 }  // namespace
 
 extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* p, const chns_solver_opts* o,
@@ -1077,9 +1172,9 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
     if (st != CHNS_OK) return st;
     if (!o || !U_old || !U) { chns_set_error("null argument"); return CHNS_EINVAL; }
     if (o->restart < 1 || o->restart > MAXSC / 4 || o->max_krylov < 1 || o->max_newton < 0 ||
-        (o->precision != 0 && o->precision != 1) || (o->pc_type < 0 || o->pc_type > 2) ||
+        (o->precision != 0 && o->precision != 1) || (o->pc_type < 0 || o->pc_type > 4) ||
         (o->pc_type >= 1 && (o->pc_degree < 2 || o->pc_degree > 200))) {
-        chns_set_error("bad solver options (restart in [1, 256], max_krylov >= 1, precision 0/1, pc_type 0/1/2, "
+        chns_set_error("bad solver options (restart in [1, 256], max_krylov >= 1, precision 0/1, pc_type 0..4, "
                        "pc_degree in [2, 200])");
         return CHNS_EINVAL;
     }
@@ -1090,7 +1185,8 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
     const int D = m->dm.dim, NF = m->dm.nf, mres = o->restart;
     const bool mixed = o->precision == 1;
     const int schur = o->pc_type >= 1 ? 1 : 0;
-    const int chblk = o->pc_type == 2 ? 1 : 0;
+    const int chblk = (o->pc_type == 2 || o->pc_type == 4) ? 1 : 0;
+    const bool use_mg = o->pc_type >= 3;   // pressure Schur by a multigrid V-cycle
     const int pcmask = schur | (chblk << 1);
     const int gE = (int)((m->dm.E + 255) / 256);
     const int gN1 = (int)((m->dm.N + 255) / 256);
@@ -1144,13 +1240,81 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
         ws->schur_gen++;   // captured applies hold the old coefficients
         return CHNS_OK;
     };
+    // geometric multigrid set-up: coarse coefficients, diagonals, Gershgorin bounds and the
+    // Chebyshev smoothers of every level (one read-back for all bounds)
+    auto mg_setup = [&]() -> chns_status {
+        if (ws->kref_dim != D) {
+            float K[64], Mr[64];
+            kref_host(D, K);
+            mref_host(D, Mr);
+            CHNS_CUDA(cudaMemcpyToSymbolAsync(c_Kref, K, sizeof(float) * (1 << D) * (1 << D), 0,
+                                              cudaMemcpyHostToDevice, c.s));
+            CHNS_CUDA(cudaMemcpyToSymbolAsync(c_Mref, Mr, sizeof(float) * (1 << D) * (1 << D), 0,
+                                              cudaMemcpyHostToDevice, c.s));
+            ws->kref_dim = D;
+        }
+        chns_status sb = mg_hier_build(m);
+        if (sb != CHNS_OK) return sb;
+        MGHier* mg = m->mg;
+        const int nl = (int)mg->lv.size();
+        for (int l = 1; l < nl; ++l) {
+            MGLevel& C = mg->lv[(size_t)l];
+            MGLevel& F = mg->lv[(size_t)l - 1];
+            CHNS_CUDA(cudaMemsetAsync(C.ce, 0, C.E * sizeof(float), c.s));
+            { mg_restrict_ce_kernel<<<(int)((F.E + 255) / 256), 256, 0, c.s>>>(F.E, D, C.fmap, F.dm.level, C.dm.level, l == 1 ? ws->ce : F.ce, C.ce); chns_count_launches(1); }
+        }
+        CHNS_CUDA(cudaMemsetAsync(mg->kmax, 0, nl * sizeof(unsigned int), c.s));
+        for (int l = 0; l < nl; ++l) {
+            MGLevel& L = mg->lv[(size_t)l];
+            const float* cel = l == 0 ? ws->ce : L.ce;
+            const int gEl = (int)((L.E + 255) / 256), gNl = (int)((L.N + 255) / 256);
+            CHNS_CUDA(cudaMemsetAsync(L.dinv, 0, L.N * sizeof(float), c.s));
+            CHNS_CUDA(cudaMemsetAsync(L.bnd, 0, L.N * sizeof(float), c.s));
+            if (D == 2) { schur_diag_kernel<2><<<gEl, 256, 0, c.s>>>(L.dm, cel, L.dinv, L.bnd); chns_count_launches(1); }
+            else { schur_diag_kernel<3><<<gEl, 256, 0, c.s>>>(L.dm, cel, L.dinv, L.bnd); chns_count_launches(1); }
+            { recip_kernel<<<gNl, 256, 0, c.s>>>(L.dinv, L.N); chns_count_launches(1); }
+            { gershgorin_max_kernel<<<grid_for(L.N), 256, 0, c.s>>>(L.bnd, L.dinv, L.N, mg->kmax + l); chns_count_launches(1); }
+        }
+        CHNS_CUDA(cudaGetLastError());
+        CHNS_CUDA(cudaMemcpyAsync(ws->hsc, mg->kmax, nl * sizeof(unsigned int), cudaMemcpyDeviceToHost, c.s));
+        CHNS_CUDA(cudaStreamSynchronize(c.s));
+        for (int l = 0; l < nl; ++l) {
+            MGLevel& L = mg->lv[(size_t)l];
+            unsigned int kbits = 0;
+            std::memcpy(&kbits, reinterpret_cast<const unsigned char*>(ws->hsc) + l * sizeof(unsigned int),
+                        sizeof(unsigned int));
+            float kb;
+            std::memcpy(&kb, &kbits, sizeof(float));
+            if (!(kb > 0.0f) || !std::isfinite(kb)) { chns_set_error("multigrid spectrum bound is not finite"); return CHNS_ENAN; }
+            const double beta = 1.01 * (double)kb;
+            if (l + 1 < nl) {
+                // smoother: damp the upper part of the spectrum of D^{-1} K
+                L.deg = o->pc_degree;
+                cheb_coeffs(beta / 10.0, beta, L.deg, L.c1, L.c2, L.inv_theta);
+            } else {
+                // coarsest level: one long sweep over the whole spectrum
+                const double nside = std::ldexp(1.0, L.mesh ? L.mesh->max_level : m->max_level);
+                L.deg = 40;
+                cheb_coeffs(beta / std::max(16.0, nside * nside / 8.0), beta, L.deg, L.c1, L.c2, L.inv_theta);
+            }
+        }
+        ws->schur_gen++;   // captured applies hold the old coefficients
+        return CHNS_OK;
+    };
     // z_p = (Chebyshev approximation of S^{-1}) v_p, strided input and output
     auto schur_apply_any = [&](auto vin, auto zout) -> chns_status {
         using TI = std::remove_const_t<std::remove_pointer_t<decltype(vin)>>;
         using TO = std::remove_pointer_t<decltype(zout)>;
         const int64_t N = m->dm.N;
-        // the apply is 2 + 2 (degree - 1) short launches: replayed from a CUDA graph
-        auto enqueue = [&](cudaStream_t st) {
+        // the apply is a sequence of short launches: replayed from a CUDA graph
+        auto enqueue = [&](cudaStream_t st) -> int {
+            if (use_mg) {
+                MGHier* mg = m->mg;
+                mg_load_kernel<TI><<<gN1, 256, 0, st>>>(N, NF, D, vin, mg->lv[0].b);
+                const int nv = mg_vcycle(mg, 0, ws->ce, st);
+                mg_store_kernel<TO><<<gN1, 256, 0, st>>>(N, NF, D, mg->lv[0].x, zout);
+                return nv + 2;
+            }
             cheb_init_kernel<TI><<<gN1, 256, 0, st>>>(N, NF, D, vin, ws->kdinv, ws->cr, ws->cx, ws->cd, ws->cy, ws->cheb_inv_theta);
             for (int k = 0; k + 1 < o->pc_degree; ++k) {
                 if (D == 2) schur_matvec_kernel<2><<<gE, 256, 0, st>>>(m->dm, ws->ce, ws->cd, ws->cy);
@@ -1158,8 +1322,8 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                 cheb_step_kernel<<<gN1, 256, 0, st>>>(N, ws->kdinv, ws->cr, ws->cx, ws->cd, ws->cy, ws->cheb_c1[k], ws->cheb_c2[k]);
             }
             cheb_final_kernel<TO><<<gN1, 256, 0, st>>>(N, NF, D, ws->cx, ws->cd, zout);
+            return 2 + 2 * (o->pc_degree - 1);
         };
-        const int nk = 2 + 2 * (o->pc_degree - 1);
         if (!ws->no_graphs) {
             SolverWS::SchurGraph* hit = nullptr;
             for (auto& g : ws->sgraph)
@@ -1174,8 +1338,9 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                 cudaGraph_t gr = nullptr;
                 bool ok = ws->cap || cudaStreamCreateWithFlags(&ws->cap, cudaStreamNonBlocking) == cudaSuccess;
                 if (ok) ok = cudaStreamBeginCapture(ws->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+                int nk_cap = 0;
                 if (ok) {
-                    enqueue(ws->cap);
+                    nk_cap = enqueue(ws->cap);
                     ok = cudaStreamEndCapture(ws->cap, &gr) == cudaSuccess && gr != nullptr;
                     if (ok) ok = cudaGraphInstantiate(&ex, gr, 0) == cudaSuccess;
                     if (gr) cudaGraphDestroy(gr);
@@ -1190,17 +1355,17 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                     slot->zout = (void*)zout;
                     slot->to = sizeof(TO);
                     slot->gen = ws->schur_gen;
+                    slot->nk = nk_cap;
                     hit = slot;
                 }
             }
             if (hit) {
                 CHNS_CUDA(cudaGraphLaunch(hit->exec, c.s));
-                chns_count_launches(nk);
+                chns_count_launches(hit->nk);
                 return CHNS_OK;
             }
         }
-        enqueue(c.s);
-        chns_count_launches(nk);
+        chns_count_launches(enqueue(c.s));
         CHNS_CUDA(cudaGetLastError());
         return CHNS_OK;
     };
@@ -1322,7 +1487,7 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
         }
         CHNS_CUDA(cudaGetLastError());
         if (schur) {
-            chns_status st3 = schur_setup();
+            chns_status st3 = use_mg ? mg_setup() : schur_setup();
             if (st3 != CHNS_OK) return st3;
         }
         if (chblk) {
