@@ -41,6 +41,8 @@ METRIC = "CHNS JÂ·x GDOF/s & % HBM roofline; mixed vs FP64 Newton step time at â
 # and DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch.  They belong to
 # the kernel sources whose SHA-256 is KERNEL_SRC_SHA; when the sources change, the bench
 # reports them as null (stale) until they are captured again.
+# preconditioner of the timed Newton step (chns_solver_opts.pc_type)
+BENCH_PC_TYPE = 1
 KERNEL_SRC_FILES = ("paper_2009_06628_gb300/csrc/element_kernels.cu", "paper_2009_06628_gb300/csrc/pointwise.cuh")
 KERNEL_SRC_SHA = "b00d8611c066543e"
 KERNEL_COUNTS = {
@@ -359,7 +361,7 @@ def run_trajectory(args):
     chns.initial_mu(gm, prm, U0)
     dof = U0.numel()
     kw = dict(rtol=1e-9, atol=1e-14, krylov_rtol=1e-3, restart=args.restart, max_krylov=args.max_krylov,
-              pc_type=args.pc_type, pc_degree=16)
+              pc_type=args.pc_type, pc_degree=args.pc_degree or (3 if args.pc_type >= 3 else 16))
     o32 = chns.SolverOpts.make(precision=1, **kw)
     o64 = chns.SolverOpts.make(precision=0, **kw)
     fields = {"v": slice(0, d), "p": slice(d, d + 1), "phi": slice(d + 1, d + 2), "mu": slice(d + 2, d + 3)}
@@ -424,8 +426,13 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--max-krylov", type=int, default=5000)
-    ap.add_argument("--pc-type", type=int, default=1)
+    ap.add_argument("--pc-type", type=int, default=None,
+                    help="preconditioner (default: 1 for the bench step and --run)")
+    ap.add_argument("--pc-degree", type=int, default=None,
+                    help="Chebyshev degree (default 16 for pc_type 1/2, 3 for the multigrid smoother of 3/4)")
     args = ap.parse_args()
+    if args.pc_type is None:
+        args.pc_type = BENCH_PC_TYPE
     if args.profile:
         return run_profile(args)
     if args.run:
@@ -452,8 +459,9 @@ def main():
     U0 = torch.tensor(U, device=dev)
     chns.initial_mu(gm, prm, U0)
     dof = U0.numel()
+    pc_kw = dict(pc_type=args.pc_type, pc_degree=args.pc_degree or (3 if args.pc_type >= 3 else 16))
     opts = chns.SolverOpts.make(rtol=1e-9, atol=1e-14, krylov_rtol=1e-3, precision=1, restart=30, max_krylov=2000,
-                                pc_type=1, pc_degree=16)
+                                **pc_kw)
     U1 = torch.empty_like(U0)
     # clock samples cover the warm-up and the timed region (the sampler starts before both)
     clocks = ClockSampler(local)
@@ -511,7 +519,7 @@ def main():
     newton = {"mixed_ms": t_ms / args.steps, "mixed_stats": stats[-1], "mixed_mass_drift": mass_drift}
     if not args.no_fp64:
         o64 = chns.SolverOpts.make(rtol=1e-9, atol=1e-14, krylov_rtol=1e-3, precision=0, restart=30, max_krylov=2000,
-                                   pc_type=1, pc_degree=16)
+                                   **pc_kw)
         U64 = torch.empty_like(U0)
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
@@ -546,6 +554,7 @@ def main():
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "elements": E, "nodes": gm.N, "dof": dof,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "preconditioner": pc_kw,
                        "l2": "inputs larger than L2 (GMRES basis 31 x 13.2 MB FP64, J x operands 26 MB, per step)"},
             "jvp_kernel": {"avg_ms": jvp_avg_ms, "launches": jvp_calls, "gdof_s": dof / (jvp_avg_ms * 1e-3) / 1e9},
             "roofline": roof, "hbm": hbm, "newton": newton, "clocks": clk, "gpu_launches": launches,

@@ -101,7 +101,8 @@ typedef struct {
                             geometric multigrid V-cycle on the octree's levels (each coarser
                             level caps the leaves one level shallower; Q1 prolongation, its
                             transpose as restriction, Jacobi-Chebyshev smoothing of degree
-                            pc_degree, a degree-40 Chebyshev sweep on the coarsest level, FP32);
+                            pc_degree, a degree-16 Chebyshev sweep on the coarsest level of at
+                            most 300 nodes or level 1, FP32);
                             4: as 3, with the Cahn-Hilliard block of 2.  The hierarchy is built
                             (host work and device memory held by the mesh) on the first call
                             that asks for it. */

@@ -293,7 +293,7 @@ chns_status mg_hier_build(chns_mesh* m) {
     while (true) {
         int deepest = 0;
         for (int8_t l : cur->h_level) deepest = std::max<int>(deepest, l);
-        if (deepest <= 1 || cur->dm.N <= 2000) break;
+        if (deepest <= 1 || cur->dm.N <= 300) break;
         const int cap = deepest - 1;
         std::vector<chns_leaf> leaves;
         std::vector<int32_t> fmap;

@@ -1294,7 +1294,7 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
             } else {
                 // coarsest level: one long sweep over the whole spectrum
                 const double nside = std::ldexp(1.0, L.mesh ? L.mesh->max_level : m->max_level);
-                L.deg = 40;
+                L.deg = 16;
                 cheb_coeffs(beta / std::max(16.0, nside * nside / 8.0), beta, L.deg, L.c1, L.c2, L.inv_theta);
             }
         }
