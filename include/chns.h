@@ -260,6 +260,30 @@ int64_t chns_transfer_nnz(const chns_transfer* t);   /* stored weights of P (-1 
 chns_status chns_transfer_apply(const chns_transfer* t, int32_t nf, int32_t transpose, const double* in,
                                 double* out, void* stream);
 
+/* Remeshing (Section 4, re-meshing and interpolation), one adaptation pass in three calls:
+ * chns_adapt_flags (device) marks every element of `mesh`: +1 (refine) where some corner
+ * value of phi (field d + 1 of U, hanging corners by their constraint means) has
+ * |phi| < phi_threshold and the element's level is below max_level; -1 (coarsening
+ * candidate) where every corner has |phi| >= phi_threshold and the level is above
+ * min_level; 0 otherwise.  U: device, N * n_f doubles; flags: device, E int8 (overwritten);
+ * asynchronous on `stream`. */
+chns_status chns_adapt_flags(const chns_mesh* mesh, const double* U, double phi_threshold, int32_t min_level,
+                             int32_t max_level, int8_t* flags, void* stream);
+
+/* chns_adapt_leaves (host only): the new leaf list.  Complete families of 2^d sibling
+ * leaves (consecutive in Morton order) whose members are all flagged -1 and deeper than
+ * min_level become their parent; leaves flagged +1 below max_level_new split into their
+ * 2^d children; then every leaf that touches (face, edge or vertex) a leaf more than one
+ * level deeper is split until the tree is 2:1 balanced (refinement only).  leaves/flags:
+ * host, n_leaves each, Morton-sorted, anchors in units of 2^-max_level.  out: host room for
+ * `capacity` leaves, Morton-sorted, anchors in units of 2^-(*out_max_level) (the deepest
+ * output level, at least 1).  *n_out receives the count; when it exceeds capacity nothing
+ * is written to out and CHNS_EINVAL is returned (call again with room for *n_out).
+ * The fields follow with chns_transfer_create(old mesh, new mesh) / chns_transfer_apply. */
+chns_status chns_adapt_leaves(int32_t dim, int32_t max_level, int64_t n_leaves, const chns_leaf* leaves,
+                              const int8_t* flags, int32_t min_level, int32_t max_level_new, chns_leaf* out,
+                              int64_t capacity, int64_t* n_out, int32_t* out_max_level);
+
 /* Host-only (no device work): the leaf list with every leaf deeper than `cap` replaced by
  * its ancestor at level `cap` (Morton order kept, duplicates merged), as the multigrid
  * hierarchy builds its coarse levels.  leaves: n_leaves Morton-sorted leaves with anchors in

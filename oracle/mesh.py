@@ -163,3 +163,20 @@ class Mesh:
                         val = val + w * self.weights[e, a, j] * U[self.parents[e, a, j]]
             out[i] = val
         return out
+
+    def adapt_flags(self, phi, thr, min_level, max_level):
+        """Remeshing flags per element (+1 refine, -1 coarsening candidate, 0 keep): an
+        element is near the interface when some corner value of phi (hanging corners: the
+        mean of their 2 or 4 parents, summed pairwise) has |phi| < thr."""
+        phi = np.asarray(phi, dtype=np.float64)
+        P, W = self.parents, self.weights
+        npar = (W > 0).sum(axis=2)                         # (E, nc): 1, 2 or 4
+        v = phi[P]                                          # (E, nc, 4)
+        corner = np.where(npar == 1, v[..., 0],
+                          np.where(npar == 2, 0.5 * (v[..., 0] + v[..., 1]),
+                                   0.25 * ((v[..., 0] + v[..., 1]) + (v[..., 2] + v[..., 3]))))
+        near = np.any(np.abs(corner) < thr, axis=1)
+        flags = np.zeros(self.E, dtype=np.int8)
+        flags[near & (self.level < max_level)] = 1
+        flags[~near & (self.level > min_level)] = -1
+        return flags

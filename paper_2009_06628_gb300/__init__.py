@@ -98,6 +98,10 @@ SIGNATURES = [
     ("chns_transfer_apply", ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P, P, P]),
     ("chns_coarsen_leaves", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, P, ctypes.c_int32, P, P,
                                            ctypes.POINTER(ctypes.c_int64)]),
+    ("chns_adapt_flags", ctypes.c_int, [P, P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, P, P]),
+    ("chns_adapt_leaves", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, P, P, ctypes.c_int32,
+                                         ctypes.c_int32, P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(ctypes.c_int32)]),
     ("chns_fma_peak", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int64, P, P]),
     ("chns_kernel_launches", ctypes.c_int64, []),
     ("chns_last_error", ctypes.c_char_p, []),
@@ -154,6 +158,7 @@ class Mesh:
         _check(L.chns_mesh_create(int(dim), int(max_level), int(leaves.shape[0]),
                                   leaves.ctypes.data_as(ctypes.c_void_p), float(lo), float(hi), ctypes.byref(h)))
         self._h = h
+        self.leaves = leaves
         self.dim = int(dim)
         self.nf = self.dim + 3
         self.max_level = int(max_level)
@@ -336,3 +341,41 @@ def coarsen_leaves(dim, max_level, leaves, cap):
                                       out.ctypes.data_as(ctypes.c_void_p), fmap.ctypes.data_as(ctypes.c_void_p),
                                       ctypes.byref(n)))
     return out[:n.value].copy(), fmap
+
+
+def adapt_flags(mesh, U, phi_threshold, min_level, max_level):
+    """Per-element int8 flags on the device: +1 refine, -1 coarsening candidate, 0 keep."""
+    flags = torch.empty(mesh.E, dtype=torch.int8, device=U.device)
+    _check(load().chns_adapt_flags(mesh.handle, _ptr(U), float(phi_threshold), int(min_level), int(max_level),
+                                   ctypes.c_void_p(flags.data_ptr()), _stream()))
+    return flags
+
+
+def adapt_leaves(dim, max_level, leaves, flags, min_level, max_level_new):
+    """Host-only: (new leaves (m, 4) int32, their max_level) after one adaptation pass."""
+    lv = np.ascontiguousarray(np.asarray(leaves, dtype=np.int32).reshape(-1, 4))
+    fl = np.ascontiguousarray(np.asarray(flags, dtype=np.int8))
+    if fl.shape[0] != lv.shape[0]:
+        raise ValueError("one flag per leaf")
+    cap = lv.shape[0] * (1 << dim) + 16
+    while True:
+        out = np.zeros((cap, 4), dtype=np.int32)
+        n, L = ctypes.c_int64(0), ctypes.c_int32(0)
+        code = load().chns_adapt_leaves(int(dim), int(max_level), lv.shape[0], lv.ctypes.data_as(ctypes.c_void_p),
+                                        fl.ctypes.data_as(ctypes.c_void_p), int(min_level), int(max_level_new),
+                                        out.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(n), ctypes.byref(L))
+        if code != 0 and n.value > cap:
+            cap = n.value
+            continue
+        _check(code)
+        return out[:n.value].copy(), int(L.value)
+
+
+def adapt(mesh, U, phi_threshold, min_level, max_level):
+    """One remeshing pass: flags from U's phi on the GPU, the new leaf list on the host, the
+    new mesh and U transferred to it by Q1 interpolation.  Returns (new mesh, new U, flags)."""
+    fl = adapt_flags(mesh, U, phi_threshold, min_level, max_level).cpu().numpy()
+    leaves, L = adapt_leaves(mesh.dim, mesh.max_level, mesh.leaves, fl, min_level, max_level)
+    new = Mesh(mesh.dim, L, leaves, mesh.lo, mesh.hi)
+    T = Transfer(mesh, new)
+    return new, T.apply(U), fl
