@@ -15,8 +15,11 @@
  *    pointers (e.g. torch CUDA tensors); "host" pointers are ordinary memory.
  *  - Independent nodes are numbered in Morton (Z) order of their integer
  *    coordinates (units of the finest cell, max_level + 1 bits per axis, x fastest).
- *  - Dirichlet rows: every velocity component of every node on the boundary of
- *    the domain cube has the row R = v^{k+1} (no-slip, Definition 1).
+ *  - Dirichlet rows: by default every velocity component of every node on the
+ *    boundary of the domain cube has the row R = v^{k+1} (no-slip, Definition 1);
+ *    chns_mesh_set_velocity_bc chooses, per face and component, Dirichlet rows
+ *    R = v^{k+1} - g with prescribed values g, or the natural condition (no row
+ *    replaced).  phi and mu always take the natural (no-flux) condition.
  *  - Pressure level (closed no-slip boxes determine p only up to a constant; the
  *    pressure rows sum to zero): params.pin_pressure = 0 keeps every row;
  *    1 replaces the pressure row of node 0 (the corner at lo^d) by p^{k+1} - p^k
@@ -142,6 +145,18 @@ int64_t chns_mesh_num_nodes(const chns_mesh* mesh);     /* independent nodes N *
 int64_t chns_mesh_num_elements(const chns_mesh* mesh);  /* leaves E */
 int64_t chns_mesh_num_hanging(const chns_mesh* mesh);   /* distinct hanging points */
 int32_t chns_mesh_dim(const chns_mesh* mesh);
+
+/* Velocity boundary conditions of the mesh (Section 5 set-ups: the lid-driven cavity's
+ * moving lid, the rising bubble's side walls with v_1 = 0 and d v_2 / d x = 0).
+ * face_mask: host, 2 * dim bytes; face 2k is the face x_k = lo, face 2k + 1 the face
+ * x_k = hi; bit c of a face's byte makes velocity component c a Dirichlet row on every
+ * node of that face (a node on several faces takes the union); a component with no bit
+ * keeps its weak-form row (natural condition).  values: device, N * dim doubles, the
+ * prescribed g (read only where a Dirichlet row is set), copied into the mesh; NULL
+ * means g = 0.  Replaces the default (all components of all boundary nodes, g = 0) for
+ * every later call on the mesh.  With pin_pressure = 2 the prescribed velocities must
+ * carry no net flux through the boundary (the pressure rows then still sum to zero). */
+chns_status chns_mesh_set_velocity_bc(chns_mesh* mesh, const uint8_t* face_mask, const double* values);
 
 /* Copy the integer coordinates of the independent nodes (units of the finest
  * cell) to host memory coords[N * dim]. */

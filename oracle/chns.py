@@ -33,8 +33,10 @@ Readings of the paper taken here (each also listed in the design notes):
   * tau's are functions of the mid-point state and are differentiated exactly.
   * Quadrature: 2-point Gauss-Legendre per axis.
   * Gravity: g_hat = -e_{d-1} (last axis); Fr <= 0 means no gravity.
-  * Dirichlet rows: every velocity component of every boundary node has the row
-    R = v^{k+1}.  Pressure level (closed no-slip boxes leave p free up to a constant;
+  * Dirichlet rows: by default every velocity component of every boundary node has
+    the row R = v^{k+1} (no-slip); with ``bc`` chosen components of chosen faces have
+    R = v^{k+1} - g and the others keep their weak-form rows (natural condition, as the
+    bubble's side walls v_1 = 0, d v_2/dx = 0).  Pressure level (closed no-slip boxes leave p free up to a constant;
     the pressure rows sum to zero, so one of them is redundant): pin_pressure = 1
     replaces row p of node 0 by p^{k+1}_0 - p^k_0 (a point value: badly conditioned);
     pin_pressure = 2 keeps every row (J then has the constant pressure as its null
@@ -117,10 +119,13 @@ class Params:
 class Oracle:
     """Element loops over a ``oracle.mesh.Mesh`` written with whole-array torch ops."""
 
-    def __init__(self, mesh, elements=None):
+    def __init__(self, mesh, elements=None, bc=None):
         """``elements`` (optional index array) restricts every element loop to a subset:
         rows of nodes whose whole support lies in the subset are then exact, which lets
-        large meshes be checked on sampled nodes."""
+        large meshes be checked on sampled nodes.  ``bc`` (optional) = (face_mask, g): the
+        velocity Dirichlet rows per face and component (face 2k: x_k = lo, 2k + 1: x_k = hi,
+        bit c: component c) and the prescribed values g (N, d) (None: zero); default: every
+        component on every boundary node, g = 0 (no-slip)."""
         self.m = mesh
         d = mesh.dim
         self.d, self.nc, self.nf = d, mesh.nc, mesh.nf
@@ -130,6 +135,23 @@ class Oracle:
         self.W = torch.tensor(mesh.weights[sel], dtype=DT)
         self.h = torch.tensor(mesh.h[sel], dtype=DT)
         self.bnd = torch.tensor(np.nonzero(mesh.boundary)[0], dtype=torch.int64)
+        d = mesh.dim
+        n_side = 1 << mesh.max_level
+        if bc is None:
+            dmask = np.repeat(mesh.boundary[:, None], d, axis=1)
+            g = np.zeros((mesh.N, d))
+        else:
+            face_mask, g = bc
+            dmask = np.zeros((mesh.N, d), dtype=bool)
+            for k in range(d):
+                for side, at in ((0, 0), (1, n_side)):
+                    on = mesh.nodes[:, k] == at
+                    for c in range(d):
+                        if (int(face_mask[2 * k + side]) >> c) & 1:
+                            dmask[on, c] = True
+            g = np.zeros((mesh.N, d)) if g is None else np.asarray(g, dtype=np.float64)
+        self.dmask = torch.tensor(dmask)
+        self.bc_g = torch.tensor(g, dtype=DT)
         # physical quadrature points (E, q, d)
         cx = torch.tensor(mesh.corner_x[sel], dtype=DT)
         self.xq = torch.einsum("qa,ead->eqd", self.N, cx)
@@ -296,7 +318,8 @@ class Oracle:
         R = self.scatter(r_loc, U_new.shape[0])
         # Dirichlet rows (no-slip) and optional pressure pin
         R = R.clone()
-        R[self.bnd, iv] = U_new[self.bnd, iv]
+        Rv = R[:, iv]
+        R[:, iv] = torch.where(self.dmask, U_new[:, iv] - self.bc_g, Rv)
         if prm.pin_pressure == 1:
             R[0, ip] = U_new[0, ip] - U_old[0, ip]
         return R

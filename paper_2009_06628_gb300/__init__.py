@@ -80,6 +80,7 @@ SIGNATURES = [
     ("chns_mesh_num_hanging", ctypes.c_int64, [P]),
     ("chns_mesh_dim", ctypes.c_int32, [P]),
     ("chns_mesh_node_coords", ctypes.c_int, [P, P]),
+    ("chns_mesh_set_velocity_bc", ctypes.c_int, [P, P, P]),
     ("chns_residual", ctypes.c_int, [P, P, P, P, P, P]),
     ("chns_jvp", ctypes.c_int, [P, P, P, P, P, P, ctypes.c_int32, P]),
     ("chns_vjp", ctypes.c_int, [P, P, P, P, P, P, P, P, P]),
@@ -175,6 +176,15 @@ class Mesh:
         out = np.zeros((self.N, self.dim), dtype=np.int32)
         _check(load().chns_mesh_node_coords(self._h, out.ctypes.data_as(ctypes.c_void_p)))
         return out
+
+    def set_velocity_bc(self, face_mask, values=None):
+        """face_mask: 2 * dim ints (face 2k: x_k = lo, 2k + 1: x_k = hi; bit c = component c
+        Dirichlet); values: optional (N, dim) FP64 CUDA tensor of prescribed velocities."""
+        fm = np.ascontiguousarray(np.asarray(face_mask, dtype=np.uint8))
+        if fm.shape != (2 * self.dim,):
+            raise ValueError("face_mask needs 2 * dim entries")
+        vp = _ptr(values.contiguous()) if values is not None else None
+        _check(load().chns_mesh_set_velocity_bc(self._h, fm.ctypes.data_as(ctypes.c_void_p), vp))
 
     def node_x(self):
         return self.lo + (self.hi - self.lo) * self.node_coords().astype(np.float64) / float(1 << self.max_level)

@@ -16,8 +16,9 @@ struct DevMesh {
     const int32_t* e2n;     // E * nc: >= 0 independent node, < 0: -(hanging index + 1)
     const int32_t* hang;    // H * 4 parent node indices; -1 marks an unused slot (edge case)
     const int8_t* level;    // E element levels
-    const uint8_t* nflag;   // N node flags, bit 0: on the domain boundary
-    const int32_t* bnodes;  // NB boundary node indices
+    const uint8_t* nflag;   // N node flags, bit k < dim: velocity component k has a Dirichlet row
+    const int32_t* bnodes;  // NB nodes with at least one Dirichlet velocity row
+    const double* bcval;    // N * dim prescribed velocities of the Dirichlet rows (null: zero)
     const int32_t* anchor;  // E * dim element anchors (units of the finest cell)
     int32_t max_level;
     double lo, hi;
@@ -42,6 +43,7 @@ struct chns_mesh {
     int8_t* d_level = nullptr;
     uint8_t* d_nflag = nullptr;
     int32_t* d_bnodes = nullptr;
+    double* d_bcval = nullptr;       // prescribed Dirichlet velocities (null: homogeneous)
     int32_t* d_anchor = nullptr;
     double* d_nmass = nullptr;       // integral of each node's basis function
     double volume = 0.0;             // |Omega|

@@ -426,18 +426,25 @@ elem_rj_kernel(DevMesh m, PCst<T> c, T inv_dt, T span,
     }
 }
 
-// Dirichlet (no-slip) rows and the pressure pin.
-//   residual: R = v^{k+1} on boundary velocity rows; R[0,p] = p^{k+1} - p^k
+// Dirichlet velocity rows and the pressure pin.
+//   residual: R = v^{k+1} - g on the Dirichlet rows (g: prescribed velocity, zero when the
+//             mesh has none); R[0,p] = p^{k+1} - p^k
 //   J x     : y = x on those rows
 template <int D, class T>
 __global__ void bc_rows_kernel(DevMesh m, const T* __restrict__ a, const T* __restrict__ b,
-                               T* __restrict__ out, int pin) {
+                               T* __restrict__ out, int pin, bool residual) {
     constexpr int NF = Shape<D>::NF;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < m.NB) {
         const int64_t n = m.bnodes[i];
+        const unsigned fl = m.nflag[n];
 #pragma unroll
-        for (int k = 0; k < D; ++k) out[n * NF + k] = a[n * NF + k];
+        for (int k = 0; k < D; ++k)
+            if ((fl >> k) & 1u) {
+                T v = a[n * NF + k];
+                if (residual && m.bcval) v -= (T)m.bcval[n * D + k];
+                out[n * NF + k] = v;
+            }
     }
     if (i == 0 && pin == 1) out[D] = b ? (a[D] - b[D]) : a[D];
 }
@@ -489,11 +496,11 @@ __global__ void __launch_bounds__(64) elem_vjp_kernel(DevMesh m, PCst<double> c,
         const double wt = (P.n == 1) ? 1.0 : (P.n == 2 ? 0.5 : 0.25);
         for (int j = 0; j < P.n; ++j) {
             const int n = P.p[j];
-            const bool bnd = m.nflag[n] & 1;
+            const unsigned fl = m.nflag[n];
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
                 double wv = __ldg(w + (size_t)n * NF + f);
-                if (f < D && bnd) wv = 0.0;
+                if (f < D && ((fl >> f) & 1u)) wv = 0.0;
                 if (f == D && pin == 1 && n == 0) wv = 0.0;
                 sw[f] += wt * wv;
             }
@@ -639,8 +646,10 @@ __global__ void bc_vjp_kernel(DevMesh m, const double* __restrict__ w, double* _
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < m.NB) {
         const int64_t n = m.bnodes[i];
+        const unsigned fl = m.nflag[n];
 #pragma unroll
-        for (int k = 0; k < D; ++k) gn[n * NF + k] += w[n * NF + k];
+        for (int k = 0; k < D; ++k)
+            if ((fl >> k) & 1u) gn[n * NF + k] += w[n * NF + k];
     }
     if (i == 0 && pin == 1) {
         gn[D] += w[D];
@@ -662,9 +671,9 @@ cudaError_t launch_rj(const chns_mesh* mm, const PhysConst& pc, const T* Uo, con
     if (err != cudaSuccess) return err;
     const int64_t nb = m.NB > 0 ? m.NB : 1;
     if (MODE == MODE_RES)
-        { bc_rows_kernel<D, T><<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(m, Un, Uo, out, pin); chns_count_launches(1); }
+        { bc_rows_kernel<D, T><<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(m, Un, Uo, out, pin, true); chns_count_launches(1); }
     else
-        { bc_rows_kernel<D, T><<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(m, x, nullptr, out, pin); chns_count_launches(1); }
+        { bc_rows_kernel<D, T><<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(m, x, nullptr, out, pin, false); chns_count_launches(1); }
     return cudaGetLastError();
 }
 

@@ -228,7 +228,7 @@ extern "C" chns_status chns_mesh_create(int32_t dim, int32_t max_level, int64_t 
             if (v == 0 || v == n_side) bnd = true;
         }
         if (bnd) {
-            nflag[n] = 1;
+            nflag[n] = (uint8_t)((1u << d) - 1u);   // no-slip: every velocity component
             bnodes.push_back((int32_t)n);
         }
     }
@@ -295,6 +295,7 @@ extern "C" chns_status chns_mesh_create(int32_t dim, int32_t max_level, int64_t 
     dm.level = m->d_level;
     dm.nflag = m->d_nflag;
     dm.bnodes = m->d_bnodes;
+    dm.bcval = nullptr;
     dm.anchor = m->d_anchor;
     dm.max_level = L;
     dm.lo = lo;
@@ -320,6 +321,7 @@ extern "C" void chns_mesh_destroy(chns_mesh* m) {
     cudaFree(m->d_level);
     cudaFree(m->d_nflag);
     cudaFree(m->d_bnodes);
+    cudaFree(m->d_bcval);
     cudaFree(m->d_anchor);
     cudaFree(m->d_nmass);
     cudaFree(m->d_partials);
@@ -336,5 +338,52 @@ extern "C" int32_t chns_mesh_dim(const chns_mesh* m) { return m ? m->dm.dim : -1
 extern "C" chns_status chns_mesh_node_coords(const chns_mesh* m, int32_t* coords) {
     if (!m || !coords) { chns_set_error("null argument"); return CHNS_EINVAL; }
     std::memcpy(coords, m->node_coords.data(), m->node_coords.size() * sizeof(int32_t));
+    return CHNS_OK;
+}
+
+extern "C" chns_status chns_mesh_set_velocity_bc(chns_mesh* m, const uint8_t* face_mask, const double* values) {
+    if (!m || !face_mask) { chns_set_error("chns_mesh_set_velocity_bc: null argument"); return CHNS_EINVAL; }
+    const int d = m->dm.dim;
+    const int64_t N = m->dm.N;
+    const int64_t side = (int64_t)1 << m->max_level;
+    for (int f = 0; f < 2 * d; ++f)
+        if (face_mask[f] >> d) { chns_set_error("chns_mesh_set_velocity_bc: a face mask has bits >= dim"); return CHNS_EINVAL; }
+    std::vector<uint8_t> nflag((size_t)N, 0);
+    std::vector<int32_t> bnodes;
+    for (int64_t n = 0; n < N; ++n) {
+        uint8_t fl = 0;
+        for (int k = 0; k < d; ++k) {
+            const int32_t c = m->node_coords[(size_t)n * d + k];
+            if (c == 0) fl |= face_mask[2 * k];
+            if (c == side) fl |= face_mask[2 * k + 1];
+        }
+        nflag[(size_t)n] = fl;
+        if (fl) bnodes.push_back((int32_t)n);
+    }
+    int32_t* nb = nullptr;
+    double* bv = nullptr;
+    cudaError_t e = cudaMalloc((void**)&nb, std::max<size_t>(bnodes.size(), 1) * sizeof(int32_t));
+    if (e == cudaSuccess && !bnodes.empty())
+        e = cudaMemcpy(nb, bnodes.data(), bnodes.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_nflag, nflag.data(), (size_t)N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && values) {
+        e = cudaMalloc((void**)&bv, (size_t)N * d * sizeof(double));
+        if (e == cudaSuccess) e = cudaMemcpy(bv, values, (size_t)N * d * sizeof(double), cudaMemcpyDeviceToDevice);
+    }
+    if (e != cudaSuccess) {
+        cudaFree(nb);
+        cudaFree(bv);
+        return chns_cuda_status(e, "chns_mesh_set_velocity_bc");
+    }
+    cudaFree(m->d_bnodes);
+    cudaFree(m->d_bcval);
+    m->d_bnodes = nb;
+    m->d_bcval = bv;
+    m->dm.bnodes = nb;
+    m->dm.bcval = bv;
+    m->dm.NB = (int64_t)bnodes.size();
+    if (m->mg) {
+        // coarse multigrid levels keep the pressure operator only; nothing to update
+    }
     return CHNS_OK;
 }

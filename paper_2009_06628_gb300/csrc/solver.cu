@@ -589,9 +589,9 @@ __global__ void pc_invert_kernel(DevMesh m, const TB* __restrict__ blk, TI* __re
             A[i][j] = (double)blk[((size_t)n * NF + i) * NF + j];
             A[i][NF + j] = (i == j) ? 1.0 : 0.0;
         }
-    const bool bnd = m.nflag[n] & 1;
+    const unsigned fl = m.nflag[n];
     for (int i = 0; i < NF; ++i) {
-        const bool idrow = (i < D && bnd) || (i == D && pin == 1 && n == 0);
+        const bool idrow = (i < D && ((fl >> i) & 1u)) || (i == D && pin == 1 && n == 0);
         if (idrow)
             for (int j = 0; j < NF; ++j) A[i][j] = (i == j) ? 1.0 : 0.0;
     }

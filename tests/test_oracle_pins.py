@@ -382,3 +382,28 @@ def test_stabilisation_parameters_spot_values(dim, level):
     # potential row: psi' at the mid-point average, -(q, mu~) + (q, psi'(phi~)), int N_a = h^d / 2
     mu_row = (pt ** 3 - pt - (c ** 3 - c)) * h ** dim / 2
     assert abs(R[node, dim + 2] - mu_row) <= 1e-12 * abs(mu_row)
+
+
+def test_velocity_boundary_conditions_rows():
+    """Mixed Dirichlet / natural velocity conditions (Section 5 set-ups): Dirichlet rows are
+    exactly v^{k+1} - g, every other row equals the row of the residual with no Dirichlet
+    row at all, and the default equals no-slip on every face."""
+    leaves = synth.uniform_leaves(2, 3)
+    m = Mesh(2, 3, leaves)
+    prm = params("drop2d", Fr=1.0, rho_ratio=3.0, eta_ratio=2.0)
+    o0, U, Un = drop_state(m, prm, perturb=1e-2)
+    g = np.stack([np.sin(np.pi * m.x[:, 0]) ** 2, 0.3 * m.x[:, 1]], axis=1)
+    # bubble side walls: v_0 Dirichlet on x = 0, 1; lid on y = 1 moving with g; y = 0 no-slip
+    fm = [1, 1, 3, 3]
+    ob = Oracle(m, bc=(fm, g))
+    on = Oracle(m, bc=([0, 0, 0, 0], None))
+    R = ob.residual(prm, U, Un).numpy()
+    Rn = on.residual(prm, U, Un).numpy()
+    mask = ob.dmask.numpy()
+    assert mask[:, 0].sum() > mask[:, 1].sum() > 0
+    vel = R[:, :2]
+    assert np.array_equal(vel[mask], (Un.numpy()[:, :2] - g)[mask])
+    assert np.array_equal(vel[~mask], Rn[:, :2][~mask])
+    assert np.array_equal(R[:, 2:], Rn[:, 2:])
+    Rd = Oracle(m, bc=([3, 3, 3, 3], None)).residual(prm, U, Un)
+    assert torch.equal(Rd, o0.residual(prm, U, Un))
