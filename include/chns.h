@@ -13,6 +13,9 @@
  *  - Vectors are caller-owned, contiguous, node-major and interleaved:
  *    U[node * n_f + field].  Pointers documented "device" must be CUDA device
  *    pointers (e.g. torch CUDA tensors); "host" pointers are ordinary memory.
+ *  - In 3D, U-type vectors read by the element kernels (U_old, U_new / U_lin, x of J x)
+ *    must start on a 16-byte (FP64) or 8-byte (FP32) boundary, as every cudaMalloc and
+ *    torch allocation does: node rows are read in pairs.  Others give CHNS_EINVAL.
  *  - Independent nodes are numbered in Morton (Z) order of their integer
  *    coordinates (units of the finest cell, max_level + 1 bits per axis, x fastest).
  *  - Dirichlet rows: by default every velocity component of every node on the

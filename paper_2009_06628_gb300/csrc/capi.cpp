@@ -33,6 +33,15 @@ int chns_num_sms() {
     return sms;
 }
 
+chns_status chns_check_rows(const chns_mesh* m, const void* p, int elem_bytes) {
+    // 3D node rows (6 values) are read as pairs: the vector must start on 2 * elem_bytes
+    if (m && m->dm.dim == 3 && p && ((uintptr_t)p % (uintptr_t)(2 * elem_bytes)) != 0) {
+        chns_set_error("3D vectors must start on a " + std::to_string(2 * elem_bytes) + "-byte boundary");
+        return CHNS_EINVAL;
+    }
+    return CHNS_OK;
+}
+
 chns_status chns_check_params(const chns_mesh* m, const chns_params* p, PhysConst* out) {
     if (!m || !p) { chns_set_error("null mesh or params"); return CHNS_EINVAL; }
     if (p->dim != m->dm.dim) { chns_set_error("params.dim differs from the mesh dimension"); return CHNS_EINVAL; }
@@ -77,6 +86,7 @@ extern "C" chns_status chns_residual(const chns_mesh* m, const chns_params* p, c
     chns_status st = chns_check_params(m, p, &pc);
     if (st != CHNS_OK) return st;
     if (!U_old || !U_new || !R) { chns_set_error("null vector"); return CHNS_EINVAL; }
+    if ((st = chns_check_rows(m, U_old, 8)) != CHNS_OK || (st = chns_check_rows(m, U_new, 8)) != CHNS_OK) return st;
     CHNS_CUDA(launch_residual(m, pc, U_old, U_new, R, p->pin_pressure, (cudaStream_t)stream));
     return CHNS_OK;
 }
@@ -87,6 +97,12 @@ extern "C" chns_status chns_jvp(const chns_mesh* m, const chns_params* p, const 
     chns_status st = chns_check_params(m, p, &pc);
     if (st != CHNS_OK) return st;
     if (!U_old || !U_lin || !x || !y) { chns_set_error("null vector"); return CHNS_EINVAL; }
+    if (precision == 0 || precision == 1) {
+        const int eb = precision == 0 ? 8 : 4;
+        if ((st = chns_check_rows(m, U_old, eb)) != CHNS_OK || (st = chns_check_rows(m, U_lin, eb)) != CHNS_OK ||
+            (st = chns_check_rows(m, x, eb)) != CHNS_OK)
+            return st;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     if (precision == 0) {
         CHNS_CUDA(launch_jvp64(m, pc, (const double*)U_old, (const double*)U_lin, (const double*)x, (double*)y,
@@ -107,6 +123,7 @@ extern "C" chns_status chns_vjp(const chns_mesh* m, const chns_params* p, const 
     chns_status st = chns_check_params(m, p, &pc);
     if (st != CHNS_OK) return st;
     if (!U_old || !U_lin || !w || !gU_new) { chns_set_error("null vector"); return CHNS_EINVAL; }
+    if ((st = chns_check_rows(m, U_old, 8)) != CHNS_OK || (st = chns_check_rows(m, U_lin, 8)) != CHNS_OK) return st;
     CHNS_CUDA(launch_vjp(m, pc, U_old, U_lin, w, gU_new, gU_old, gCn, p->pin_pressure, (cudaStream_t)stream));
     return CHNS_OK;
 }

@@ -70,6 +70,8 @@ struct PhysConst {
 void chns_set_error(const std::string& msg);
 chns_status chns_cuda_status(cudaError_t err, const char* where);
 chns_status chns_check_params(const chns_mesh* mesh, const chns_params* p, PhysConst* out);
+// 3D node rows are read in pairs: CHNS_EINVAL unless p is 2 * elem_bytes aligned
+chns_status chns_check_rows(const chns_mesh* mesh, const void* p, int elem_bytes);
 
 #define CHNS_CUDA(call)                                                   \
     do {                                                                  \

@@ -70,6 +70,34 @@ __device__ __forceinline__ Basis<D, T> basis(int a, int q, T inv_h) {
 template <class T>
 __device__ __forceinline__ T clip1(T x) { return x > T(1) ? T(1) : (x < T(-1) ? T(-1) : x); }
 
+// Shared-memory vector loads of the 3D corner / flux rows (fewer load instructions; the
+// rows are laid out so every pair starts on an 8-byte (FP32) or 16-byte (FP64) boundary)
+template <class T> struct Pair;
+template <> struct Pair<float> { using type = float2; };
+template <> struct Pair<double> { using type = double2; };
+template <class T>
+__device__ __forceinline__ typename Pair<T>::type ld_pair(const T* p) {
+    return *reinterpret_cast<const typename Pair<T>::type*>(p);
+}
+
+// A node row of NF values from global memory (read-only path).  In 3D a row is 24 B
+// (FP32) or 48 B (FP64) at node * row, so it is read as three 8- or 16-byte pairs.
+template <int D, class T>
+__device__ __forceinline__ void ld_row(const T* __restrict__ p, T v[Shape<D>::NF]) {
+    if constexpr (D == 3) {
+        const typename Pair<T>::type* q = reinterpret_cast<const typename Pair<T>::type*>(p);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const typename Pair<T>::type t = __ldg(q + i);
+            v[2 * i] = t.x;
+            v[2 * i + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int f = 0; f < Shape<D>::NF; ++f) v[f] = __ldg(p + f);
+    }
+}
+
 // element size (hi - lo) 2^-level, exact in the working precision (no FP64 work in
 // the FP32 kernels: GB300's FP64 pipe is 1/64 of its FP32 rate)
 __device__ __forceinline__ float scale_pow2(float span, int lev) { return ldexpf(span, -lev); }
@@ -100,7 +128,7 @@ __device__ __forceinline__ Parents parents_of(const DevMesh& m, int ent) {
 
 // Primal corner data of one element in shared memory.
 template <int D, class T>
-struct CornerPrimal {
+struct __align__(16) CornerPrimal {
     T ut[Shape<D>::NC][Shape<D>::NF];   // mid-point average
     T dd[Shape<D>::NC][D + 1];          // (new - old) for v and phi
     T ps[Shape<D>::NC];                 // phi* (clip at independent nodes, interpolated)
@@ -122,10 +150,10 @@ __device__ __forceinline__ unsigned gather_primal(const DevMesh& m, const Parent
         const T* po = Uo + (size_t)P.p[j] * NF;
         const T* pn = Un + (size_t)P.p[j] * NF;
         T o[NF], n[NF];
+        ld_row<D, T>(po, o);
+        ld_row<D, T>(pn, n);
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-            o[f] = __ldg(po + f);
-            n[f] = __ldg(pn + f);
             so[f] += w * o[f];
             sn[f] += w * n[f];
         }
@@ -217,29 +245,63 @@ __device__ __forceinline__ void interp_primal(const CornerPrimal<D, T>& C, int q
     T w[3];
     gauss_weights<T>(q, w);
     T g[D], val;
+    if constexpr (D == 3) {
+        // 3D rows hold 6 fields and 4 differences: read them two at a time
+        typename Pair<T>::type c[Shape<D>::NC];
 #pragma unroll
-    for (int i = 0; i < D; ++i) {
-        sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return C.ut[a][i]; }, val, g, nullptr);
-        X.v[i] = val;
+        for (int a = 0; a < Shape<D>::NC; ++a) c[a] = ld_pair(&C.ut[a][0]);
+        sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return c[a].x; }, X.v[0], X.gv[0], nullptr);
+        sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return c[a].y; }, X.v[1], X.gv[1], nullptr);
 #pragma unroll
-        for (int k = 0; k < D; ++k) X.gv[i][k] = g[k];
+        for (int a = 0; a < Shape<D>::NC; ++a) c[a] = ld_pair(&C.ut[a][2]);
+        sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return c[a].x; }, X.v[2], X.gv[2], nullptr);
+        sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return c[a].y; }, X.p, X.gp, nullptr);
+#pragma unroll
+        for (int a = 0; a < Shape<D>::NC; ++a) c[a] = ld_pair(&C.ut[a][4]);
+        sf_vgrad<D, true, T>(w, inv_h, [&](int a) { return c[a].x; }, X.phi, X.gphi, X.H);
+        sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return c[a].y; }, X.mu, X.gmu, nullptr);
+        sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return C.ps[a]; }, X.ps, X.gps, nullptr);
+        T div = X.gv[0][0] + X.gv[1][1] + X.gv[2][2];
+#pragma unroll
+        for (int a = 0; a < Shape<D>::NC; ++a) c[a] = ld_pair(&C.dd[a][0]);
+        sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return c[a].x; }, val, g, nullptr);
+        X.vdt[0] = val * inv_dt;
+        div += T(0.5) * g[0];
+        sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return c[a].y; }, val, g, nullptr);
+        X.vdt[1] = val * inv_dt;
+        div += T(0.5) * g[1];
+#pragma unroll
+        for (int a = 0; a < Shape<D>::NC; ++a) c[a] = ld_pair(&C.dd[a][2]);
+        sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return c[a].x; }, val, g, nullptr);
+        X.vdt[2] = val * inv_dt;
+        div += T(0.5) * g[2];
+        X.divnew = div;
+        X.phidt = sf_value<D, T>(w, [&](int a) { return c[a].y; }) * inv_dt;
+    } else {
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return C.ut[a][i]; }, val, g, nullptr);
+            X.v[i] = val;
+#pragma unroll
+            for (int k = 0; k < D; ++k) X.gv[i][k] = g[k];
+        }
+        sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return C.ut[a][D]; }, X.p, X.gp, nullptr);
+        sf_vgrad<D, true, T>(w, inv_h, [&](int a) { return C.ut[a][D + 1]; }, X.phi, X.gphi, X.H);
+        sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return C.ut[a][D + 2]; }, X.mu, X.gmu, nullptr);
+        sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return C.ps[a]; }, X.ps, X.gps, nullptr);
+        // div v^{k+1} = div v~ + (1/2) div (v^{k+1} - v^k)
+        T div = X.gv[0][0];
+#pragma unroll
+        for (int i = 1; i < D; ++i) div += X.gv[i][i];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return C.dd[a][i]; }, val, g, nullptr);
+            X.vdt[i] = val * inv_dt;
+            div += T(0.5) * g[i];
+        }
+        X.divnew = div;
+        X.phidt = sf_value<D, T>(w, [&](int a) { return C.dd[a][D]; }) * inv_dt;
     }
-    sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return C.ut[a][D]; }, X.p, X.gp, nullptr);
-    sf_vgrad<D, true, T>(w, inv_h, [&](int a) { return C.ut[a][D + 1]; }, X.phi, X.gphi, X.H);
-    sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return C.ut[a][D + 2]; }, X.mu, X.gmu, nullptr);
-    sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return C.ps[a]; }, X.ps, X.gps, nullptr);
-    // div v^{k+1} = div v~ + (1/2) div (v^{k+1} - v^k)
-    T div = X.gv[0][0];
-#pragma unroll
-    for (int i = 1; i < D; ++i) div += X.gv[i][i];
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-        sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return C.dd[a][i]; }, val, g, nullptr);
-        X.vdt[i] = val * inv_dt;
-        div += T(0.5) * g[i];
-    }
-    X.divnew = div;
-    X.phidt = sf_value<D, T>(w, [&](int a) { return C.dd[a][D]; }) * inv_dt;
 }
 
 template <class R>
@@ -270,13 +332,38 @@ __host__ __device__ PCst<R> make_pcst(const PhysConst& pc) {
 template <int D, class T>
 __device__ __forceinline__ void contract(const T (*sf)[Shape<D>::NF * (D + 1)], int a, T inv_h,
                                          T r[Shape<D>::NF]) {
-    constexpr int NF = Shape<D>::NF;
+    constexpr int NF = Shape<D>::NF, NS = NF * (D + 1);
 #pragma unroll
     for (int f = 0; f < NF; ++f) r[f] = T(0);
 #pragma unroll
     for (int q = 0; q < Shape<D>::NC; ++q) {
         const Basis<D, T> b = basis<D, T>(a, q, inv_h);
-        const T* s = sf[q];
+        T s[NS];
+        if constexpr (D == 3) {
+            // the 24 fluxes of a Gauss point in 16-byte shared loads (rows are 16-byte aligned)
+            if constexpr (sizeof(T) == 4) {
+                const float4* v = reinterpret_cast<const float4*>(sf[q]);
+#pragma unroll
+                for (int i = 0; i < NS / 4; ++i) {
+                    const float4 t = v[i];
+                    s[4 * i] = t.x;
+                    s[4 * i + 1] = t.y;
+                    s[4 * i + 2] = t.z;
+                    s[4 * i + 3] = t.w;
+                }
+            } else {
+                const double2* v = reinterpret_cast<const double2*>(sf[q]);
+#pragma unroll
+                for (int i = 0; i < NS / 2; ++i) {
+                    const double2 t = v[i];
+                    s[2 * i] = t.x;
+                    s[2 * i + 1] = t.y;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < NS; ++i) s[i] = sf[q][i];
+        }
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             T acc = b.N * s[f];
@@ -304,11 +391,11 @@ __device__ __forceinline__ void scatter_add(T* __restrict__ out, const Parents& 
 enum { MODE_RES = 0, MODE_JVP = 1 };
 
 template <int D, class T, int MODE>
-struct SmemRJ {
+struct __align__(16) SmemRJ {
     CornerPrimal<D, T> cp;
-    T x[MODE == MODE_JVP ? Shape<D>::NC : 1][Shape<D>::NF];   // tangent corner values
-    T xps[MODE == MODE_JVP ? Shape<D>::NC : 1];               // tangent of phi*
-    T f[Shape<D>::NC][Shape<D>::NF * (D + 1)];                // fluxes per Gauss point
+    __align__(16) T x[MODE == MODE_JVP ? Shape<D>::NC : 1][Shape<D>::NF];   // tangent corner values
+    T xps[MODE == MODE_JVP ? Shape<D>::NC : 1];                             // tangent of phi*
+    __align__(16) T f[Shape<D>::NC][Shape<D>::NF * (D + 1)];                // fluxes per Gauss point
 };
 
 template <int D, class T, int MODE>
@@ -319,7 +406,7 @@ elem_rj_kernel(DevMesh m, PCst<T> c, T inv_dt, T span,
                                                       const T* __restrict__ xin, T* __restrict__ out,
                                                       unsigned int* __restrict__ flags) {
     constexpr int NC = Shape<D>::NC, NF = Shape<D>::NF, EPB = Shape<D>::EPB;
-    __shared__ SmemRJ<D, T, MODE> sm[EPB];
+    __shared__ __align__(16) SmemRJ<D, T, MODE> sm[EPB];
     const int le = threadIdx.x / NC;
     const int t = threadIdx.x % NC;
     const int64_t e = (int64_t)blockIdx.x * EPB + le;
@@ -343,10 +430,11 @@ elem_rj_kernel(DevMesh m, PCst<T> c, T inv_dt, T span,
             for (int f = 0; f < NF; ++f) sx[f] = T(0);
             const T w = (P.n == 1) ? T(1) : (P.n == 2 ? T(0.5) : T(0.25));
             for (int j = 0; j < P.n; ++j) {
-                const T* px = xin + (size_t)P.p[j] * NF;
+                T xr[NF];
+                ld_row<D, T>(xin + (size_t)P.p[j] * NF, xr);
 #pragma unroll
-                for (int f = 0; f < NF; ++f) sx[f] += w * __ldg(px + f);
-                if (mask & (1u << j)) xps += w * T(0.5) * __ldg(px + D + 1);
+                for (int f = 0; f < NF; ++f) sx[f] += w * xr[f];
+                if (mask & (1u << j)) xps += w * T(0.5) * xr[D + 1];
             }
 #pragma unroll
             for (int f = 0; f < NF; ++f) S.x[t][f] = sx[f];
@@ -377,12 +465,27 @@ elem_rj_kernel(DevMesh m, PCst<T> c, T inv_dt, T span,
             {
                 T w[3];
                 gauss_weights<T>(q, w);
+                if constexpr (D == 3) {
+                    // tangent corner rows two fields at a time
+                    typename Pair<T>::type c[NC];
 #pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    if (f == D + 1)
-                        sf_vgrad<D, true, T>(w, inv_h, [&](int a) { return S.x[a][f]; }, xv[f], xg[f], xH);
-                    else
-                        sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return S.x[a][f]; }, xv[f], xg[f], nullptr);
+                    for (int f = 0; f < NF; f += 2) {
+#pragma unroll
+                        for (int a = 0; a < NC; ++a) c[a] = ld_pair(&S.x[a][f]);
+                        if (f == D + 1)
+                            sf_vgrad<D, true, T>(w, inv_h, [&](int a) { return c[a].x; }, xv[f], xg[f], xH);
+                        else
+                            sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return c[a].x; }, xv[f], xg[f], nullptr);
+                        sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return c[a].y; }, xv[f + 1], xg[f + 1], nullptr);
+                    }
+                } else {
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        if (f == D + 1)
+                            sf_vgrad<D, true, T>(w, inv_h, [&](int a) { return S.x[a][f]; }, xv[f], xg[f], xH);
+                        else
+                            sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return S.x[a][f]; }, xv[f], xg[f], nullptr);
+                    }
                 }
                 sf_vgrad<D, false, T>(w, inv_h, [&](int a) { return S.xps[a]; }, xpsv, xpsg, nullptr);
             }

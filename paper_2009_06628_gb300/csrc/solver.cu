@@ -1171,6 +1171,7 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
     chns_status st = chns_check_params(mc, p, &pc);
     if (st != CHNS_OK) return st;
     if (!o || !U_old || !U) { chns_set_error("null argument"); return CHNS_EINVAL; }
+    if ((st = chns_check_rows(mc, U_old, 8)) != CHNS_OK || (st = chns_check_rows(mc, U, 8)) != CHNS_OK) return st;
     if (o->restart < 1 || o->restart > MAXSC / 4 || o->max_krylov < 1 || o->max_newton < 0 ||
         (o->precision != 0 && o->precision != 1) || (o->pc_type < 0 || o->pc_type > 4) ||
         (o->pc_type >= 1 && (o->pc_degree < 2 || o->pc_degree > 200))) {
@@ -1873,6 +1874,7 @@ extern "C" chns_status chns_step_adjoint(const chns_mesh* mc, const chns_params*
     chns_status st = chns_check_params(mc, p, &pc);
     if (st != CHNS_OK) return st;
     if (!o || !U_old || !U_new || !g || !lambda || !gU_old) { chns_set_error("null argument"); return CHNS_EINVAL; }
+    if ((st = chns_check_rows(mc, U_old, 8)) != CHNS_OK || (st = chns_check_rows(mc, U_new, 8)) != CHNS_OK) return st;
     if (o->restart < 1 || o->restart > MAXSC / 4 || o->max_krylov < 1) {
         chns_set_error("bad solver options (restart in [1, 256], max_krylov >= 1)");
         return CHNS_EINVAL;

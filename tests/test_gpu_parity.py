@@ -231,3 +231,23 @@ def test_fma_peak_probe(chns):
     f64 = chns.fma_peak(0, 2000)
     assert 40e12 < f32 < 82e12, f32
     assert 0.1e12 < f64 < f32 / 8, (f64, f32)
+
+
+def test_misaligned_3d_rows_are_rejected(chns):
+    """3D node rows are read in pairs, so a vector that does not start on a 16-byte (FP64)
+    or 8-byte (FP32) boundary is refused on the host before any kernel runs."""
+    import ctypes
+    level = 2
+    gm = chns.Mesh(3, level, synth.uniform_leaves(3, level))
+    prm = chns.Params.make(**synth.config_params("drop3d"))
+    n = gm.N * 6
+    buf = torch.zeros(2 * n + 4, dtype=torch.float64, device="cuda")
+    good = ctypes.c_void_p(buf.data_ptr())
+    bad = ctypes.c_void_p(buf.data_ptr() + 8)
+    out = ctypes.c_void_p(buf.data_ptr() + 8 * (n + 2))
+    lib = chns.load()
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.chns_residual(gm.handle, ctypes.byref(prm), bad, good, out, s) == 1
+    assert lib.chns_jvp(gm.handle, ctypes.byref(prm), good, bad, good, out, 0, s) == 1
+    assert lib.chns_residual(gm.handle, ctypes.byref(prm), good, good, out, s) == 0
+    torch.cuda.synchronize()
