@@ -317,6 +317,7 @@ def run_profile(args):
     """One kernel of the hot path, --reps launches, on the chosen mesh."""
     import paper_2009_06628_gb300 as chns
     gm, cfg, U = workload_mesh(chns, args)
+    gm.set_scatter(args.scatter)
     prm = chns.Params.make(**cfg)
     U0 = torch.tensor(U, device="cuda")
     Un = U0 + 1e-4 * torch.randn(U0.shape, device="cuda", dtype=torch.float64,
@@ -344,6 +345,7 @@ def run_profile(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.reps
     print(json.dumps({"profile": args.profile, "mesh": args.mesh, "level": args.level, "elements": gm.E, "nodes": gm.N,
+                      "scatter": args.scatter, "colours": gm.num_colours,
                       "avg_ms_per_call": ms, "gdof_s": U0.numel() / (ms * 1e-3) / 1e9}))
     return 0
 
@@ -420,6 +422,8 @@ def main():
     ap.add_argument("--level", type=int, default=LEVEL)
     ap.add_argument("--mesh", choices=["uniform", "twodrops", "twodrops_l7", "layer", "layer_l8"], default="uniform")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--scatter", type=int, default=0, choices=[0, 1, 2],
+                    help="element scatter for --profile: 0 atomics, 1 colouring, 2 warp-aggregated")
     ap.add_argument("--run", action="store_true",
                     help="multi-step Newton run on --mesh (mixed, and FP64 for --fp64-steps) instead of the bench")
     ap.add_argument("--newton-steps", type=int, default=5)

@@ -161,6 +161,18 @@ int32_t chns_mesh_dim(const chns_mesh* mesh);
  * carry no net flux through the boundary (the pressure rows then still sum to zero). */
 chns_status chns_mesh_set_velocity_bc(chns_mesh* mesh, const uint8_t* face_mask, const double* values);
 
+/* Scatter strategy of the element kernels (residual, J x, J^T w) on this mesh: how element
+ * rows are added into node rows (hanging corners folded into their parents).
+ * mode 0: atomic adds (default); 1: element colouring -- elements are greedily coloured
+ * (Morton order) so that no two elements of a colour share a node, one launch per colour
+ * with plain adds: every node sums its contributions in a fixed order, so results are
+ * bit-identical from run to run (the d/dCn scalar of chns_vjp still uses an atomic);
+ * 2: warp-aggregated atomics (lanes of a warp that target one node add in shared memory
+ * first; J^T w uses mode 0 there).  The colouring is built on the host at the first call
+ * with mode 1.  CHNS_EINVAL for another mode. */
+chns_status chns_mesh_set_scatter(chns_mesh* mesh, int32_t mode);
+int32_t chns_mesh_num_colours(const chns_mesh* mesh);   /* 0 until mode 1 was set */
+
 /* Copy the integer coordinates of the independent nodes (units of the finest
  * cell) to host memory coords[N * dim]. */
 chns_status chns_mesh_node_coords(const chns_mesh* mesh, int32_t* coords);

@@ -81,6 +81,8 @@ SIGNATURES = [
     ("chns_mesh_dim", ctypes.c_int32, [P]),
     ("chns_mesh_node_coords", ctypes.c_int, [P, P]),
     ("chns_mesh_set_velocity_bc", ctypes.c_int, [P, P, P]),
+    ("chns_mesh_set_scatter", ctypes.c_int, [P, ctypes.c_int32]),
+    ("chns_mesh_num_colours", ctypes.c_int32, [P]),
     ("chns_residual", ctypes.c_int, [P, P, P, P, P, P]),
     ("chns_jvp", ctypes.c_int, [P, P, P, P, P, P, ctypes.c_int32, P]),
     ("chns_vjp", ctypes.c_int, [P, P, P, P, P, P, P, P, P]),
@@ -185,6 +187,14 @@ class Mesh:
             raise ValueError("face_mask needs 2 * dim entries")
         vp = _ptr(values.contiguous()) if values is not None else None
         _check(load().chns_mesh_set_velocity_bc(self._h, fm.ctypes.data_as(ctypes.c_void_p), vp))
+
+    def set_scatter(self, mode):
+        """0 atomics, 1 element colouring (deterministic), 2 warp-aggregated atomics."""
+        _check(load().chns_mesh_set_scatter(self._h, int(mode)))
+
+    @property
+    def num_colours(self):
+        return int(load().chns_mesh_num_colours(self._h))
 
     def node_x(self):
         return self.lo + (self.hi - self.lo) * self.node_coords().astype(np.float64) / float(1 << self.max_level)

@@ -54,6 +54,10 @@ struct chns_mesh {
     unsigned int* d_flags = nullptr; // bit 0: a tau radicand was not positive
     SolverWS* ws = nullptr;
     MGHier* mg = nullptr;
+    // scatter strategy of the element kernels (0 atomics, 1 colouring, 2 warp-aggregated)
+    int32_t scatter = 0;
+    int32_t* d_elist = nullptr;          // elements sorted by colour (Morton order within one)
+    std::vector<int64_t> colour_off;     // colour k: d_elist[colour_off[k] .. colour_off[k + 1])
 };
 
 // Kernel-side parameter block derived from chns_params (all FP64; kernels cast).

@@ -11,6 +11,8 @@
 // parent nodes; the scatter applies the transpose (the same weights).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "chns_internal.h"
 #include "pointwise.cuh"
 
@@ -374,14 +376,62 @@ __device__ __forceinline__ void contract(const T (*sf)[Shape<D>::NF * (D + 1)], 
     }
 }
 
-template <int D, class T>
+// Scatter strategies of the element kernels (chns_mesh_set_scatter):
+//   SCAT_ATOMIC  one atomic add per corner row entry and parent (default);
+//   SCAT_PLAIN   plain read-modify-write, for launches over one colour of an element
+//                colouring (no two elements of a colour share a node): deterministic;
+//   SCAT_WARPAGG the lanes of a warp that target the same node (found with
+//                __match_any_sync) add their rows in shared memory first and one lane
+//                issues the atomics.
+enum { SCAT_ATOMIC = 0, SCAT_PLAIN = 1, SCAT_WARPAGG = 2 };
+
+template <int D, class T, int SCAT>
 __device__ __forceinline__ void scatter_add(T* __restrict__ out, const Parents& P, const T r[Shape<D>::NF]) {
     constexpr int NF = Shape<D>::NF;
     const T w = (P.n == 1) ? T(1) : (P.n == 2 ? T(0.5) : T(0.25));
     for (int j = 0; j < P.n; ++j) {
         T* o = out + (size_t)P.p[j] * NF;
 #pragma unroll
-        for (int f = 0; f < NF; ++f) atomicAdd(o + f, w * r[f]);
+        for (int f = 0; f < NF; ++f) {
+            if (SCAT == SCAT_PLAIN)
+                o[f] += w * r[f];
+            else
+                atomicAdd(o + f, w * r[f]);
+        }
+    }
+}
+
+// Warp-aggregated scatter: every lane of the warp calls it (valid == false: no rows).
+// wbuf: this warp's 32 x NF shared staging rows.
+template <int D, class T>
+__device__ __forceinline__ void scatter_add_warpagg(T* __restrict__ out, const Parents& P, const T r[Shape<D>::NF],
+                                                    bool valid, T (*wbuf)[Shape<D>::NF]) {
+    constexpr int NF = Shape<D>::NF;
+    const int lane = threadIdx.x & 31;
+    const T w = (P.n == 1) ? T(1) : (P.n == 2 ? T(0.5) : T(0.25));
+#pragma unroll 1
+    for (int j = 0; j < 4; ++j) {
+        const int node = (valid && j < P.n) ? P.p[j] : -1;
+        if (node >= 0) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) wbuf[lane][f] = w * r[f];
+        }
+        __syncwarp();
+        const unsigned grp = __match_any_sync(0xffffffffu, node);
+        if (node >= 0 && lane == __ffs(grp) - 1) {
+            T acc[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) acc[f] = T(0);
+            for (unsigned g = grp; g; g &= g - 1) {
+                const int src = __ffs(g) - 1;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) acc[f] += wbuf[src][f];
+            }
+            T* o = out + (size_t)node * NF;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) atomicAdd(o + f, acc[f]);
+        }
+        __syncwarp();
     }
 }
 
@@ -398,19 +448,23 @@ struct __align__(16) SmemRJ {
     __align__(16) T f[Shape<D>::NC][Shape<D>::NF * (D + 1)];                // fluxes per Gauss point
 };
 
-template <int D, class T, int MODE>
+template <int D, class T, int MODE, int SCAT>
 __global__ void __launch_bounds__(128, (MODE == MODE_JVP && sizeof(T) == 4) ? 5 : 1)
 elem_rj_kernel(DevMesh m, PCst<T> c, T inv_dt, T span,
                                                       const T* __restrict__ Uo,
                                                       const T* __restrict__ Un,
                                                       const T* __restrict__ xin, T* __restrict__ out,
-                                                      unsigned int* __restrict__ flags) {
+                                                      unsigned int* __restrict__ flags,
+                                                      const int32_t* __restrict__ elist, int64_t ecount) {
     constexpr int NC = Shape<D>::NC, NF = Shape<D>::NF, EPB = Shape<D>::EPB;
     __shared__ __align__(16) SmemRJ<D, T, MODE> sm[EPB];
+    __shared__ T wbuf[SCAT == SCAT_WARPAGG ? 4 : 1][32][NF];
     const int le = threadIdx.x / NC;
     const int t = threadIdx.x % NC;
-    const int64_t e = (int64_t)blockIdx.x * EPB + le;
-    const bool valid = e < m.E;
+    // element: the idx-th of the launch (elist: the listed elements of one colour)
+    const int64_t idx = (int64_t)blockIdx.x * EPB + le;
+    const bool valid = idx < ecount;
+    const int64_t e = valid ? (elist ? (int64_t)elist[idx] : idx) : 0;
     SmemRJ<D, T, MODE>& S = sm[le];
 
     Parents P;
@@ -522,10 +576,24 @@ elem_rj_kernel(DevMesh m, PCst<T> c, T inv_dt, T span,
         }
     }
     __syncwarp();
-    if (valid) {
+    if (SCAT == SCAT_WARPAGG) {
+        T r[NF];
+        if (valid) contract<D, T>(S.f, t, inv_h, r);
+        scatter_add_warpagg<D, T>(out, P, r, valid, wbuf[(threadIdx.x >> 5) & 3]);
+    } else if (SCAT == SCAT_PLAIN) {
+        // corners of one element can share a parent node (hanging corners): they add one
+        // after another, in corner order; elements of one colour share no node
+        T r[NF];
+        if (valid) contract<D, T>(S.f, t, inv_h, r);
+#pragma unroll 1
+        for (int a = 0; a < NC; ++a) {
+            if (valid && t == a) scatter_add<D, T, SCAT_PLAIN>(out, P, r);
+            __syncwarp();
+        }
+    } else if (valid) {
         T r[NF];
         contract<D, T>(S.f, t, inv_h, r);
-        scatter_add<D, T>(out, P, r);
+        scatter_add<D, T, SCAT>(out, P, r);
     }
 }
 
@@ -568,18 +636,20 @@ struct SmemVJP {
     double xb[Shape<D>::NC][NXb<D>::n];
 };
 
-template <int D>
+template <int D, int SCAT>
 __global__ void __launch_bounds__(64) elem_vjp_kernel(DevMesh m, PCst<double> c, double Cn, double inv_dt,
                                                       const double* __restrict__ Uo,
                                                       const double* __restrict__ Un,
                                                       const double* __restrict__ w, double* __restrict__ gn,
-                                                      double* __restrict__ go, double* __restrict__ gCn, int pin) {
+                                                      double* __restrict__ go, double* __restrict__ gCn, int pin,
+                                                      const int32_t* __restrict__ elist, int64_t ecount) {
     constexpr int NC = Shape<D>::NC, NF = Shape<D>::NF, NH = Shape<D>::NH, EPB = 64 / NC;
     __shared__ SmemVJP<D> sm[EPB];
     const int le = threadIdx.x / NC;
     const int t = threadIdx.x % NC;
-    const int64_t e = (int64_t)blockIdx.x * EPB + le;
-    const bool valid = e < m.E;
+    const int64_t idx = (int64_t)blockIdx.x * EPB + le;
+    const bool valid = idx < ecount;
+    const int64_t e = valid ? (elist ? (int64_t)elist[idx] : idx) : 0;
     SmemVJP<D>& S = sm[le];
     Parents P;
     P.n = 0;
@@ -666,10 +736,11 @@ __global__ void __launch_bounds__(64) elem_vjp_kernel(DevMesh m, PCst<double> c,
         for (int i = 0; i < D; ++i) o[k++] = Xb.gps[i];
     }
     __syncwarp();
+    double rn[NF], ro[NF], psb = 0.0;
     if (valid) {
         // transpose of the interpolation for corner a = t
         const int a = t;
-        double ut[NF], ddv[D + 1], divb[D], psb = 0.0;
+        double ut[NF], ddv[D + 1], divb[D];
 #pragma unroll
         for (int f = 0; f < NF; ++f) ut[f] = 0.0;
 #pragma unroll
@@ -710,7 +781,6 @@ __global__ void __launch_bounds__(64) elem_vjp_kernel(DevMesh m, PCst<double> c,
         }
         // corner adjoints of U^{k+1} and U^k: averages take 1/2 each, differences +-1/dt,
         // div v^{k+1} acts on the new level only
-        double rn[NF], ro[NF];
 #pragma unroll
         for (int f = 0; f < NF; ++f) rn[f] = ro[f] = 0.5 * ut[f];
 #pragma unroll
@@ -720,17 +790,32 @@ __global__ void __launch_bounds__(64) elem_vjp_kernel(DevMesh m, PCst<double> c,
         }
         rn[D + 1] += inv_dt * ddv[D];
         ro[D + 1] -= inv_dt * ddv[D];
+    }
+    {
         const double wt = (P.n == 1) ? 1.0 : (P.n == 2 ? 0.5 : 0.25);
-        for (int j = 0; j < P.n; ++j) {
-            double* on = gn + (size_t)P.p[j] * NF;
-            double* oo = go ? go + (size_t)P.p[j] * NF : nullptr;
-            const double pst = (mask & (1u << j)) ? 0.5 * psb : 0.0;
+        // plain adds (colouring): the corners of an element add one after another (two
+        // corners can share a constraint parent); elements of one colour share no node
+#pragma unroll 1
+        for (int a = 0; a < (SCAT == SCAT_PLAIN ? NC : 1); ++a) {
+            if (valid && (SCAT != SCAT_PLAIN || t == a)) {
+                for (int j = 0; j < P.n; ++j) {
+                    double* on = gn + (size_t)P.p[j] * NF;
+                    double* oo = go ? go + (size_t)P.p[j] * NF : nullptr;
+                    const double pst = (mask & (1u << j)) ? 0.5 * psb : 0.0;
 #pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                const double extra = (f == D + 1) ? pst : 0.0;
-                atomicAdd(on + f, wt * (rn[f] + extra));
-                if (oo) atomicAdd(oo + f, wt * (ro[f] + extra));
+                    for (int f = 0; f < NF; ++f) {
+                        const double extra = (f == D + 1) ? pst : 0.0;
+                        if (SCAT == SCAT_PLAIN) {
+                            on[f] += wt * (rn[f] + extra);
+                            if (oo) oo[f] += wt * (ro[f] + extra);
+                        } else {
+                            atomicAdd(on + f, wt * (rn[f] + extra));
+                            if (oo) atomicAdd(oo + f, wt * (ro[f] + extra));
+                        }
+                    }
+                }
             }
+            if (SCAT == SCAT_PLAIN) __syncwarp();
         }
     }
     if (gCn) {
@@ -768,8 +853,26 @@ cudaError_t launch_rj(const chns_mesh* mm, const PhysConst& pc, const T* Uo, con
     cudaError_t err = cudaMemsetAsync(out, 0, bytes, s);
     if (err != cudaSuccess) return err;
     const int EPB = Shape<D>::EPB;
-    const int64_t blocks = (m.E + EPB - 1) / EPB;
-    { elem_rj_kernel<D, T, MODE><<<(unsigned)blocks, EPB * Shape<D>::NC, 0, s>>>( m, make_pcst<T>(pc), T(pc.inv_dt), T(m.hi - m.lo), Uo, Un, x, out, mm->d_flags); chns_count_launches(1); }
+    const PCst<T> c = make_pcst<T>(pc);
+    if (mm->scatter == SCAT_PLAIN) {
+        // one launch per colour of the element colouring, fixed order: deterministic sums
+        for (size_t k = 0; k + 1 < mm->colour_off.size(); ++k) {
+            const int64_t c0 = mm->colour_off[k], cnt = mm->colour_off[k + 1] - c0;
+            if (cnt <= 0) continue;
+            elem_rj_kernel<D, T, MODE, SCAT_PLAIN><<<(unsigned)((cnt + EPB - 1) / EPB), EPB * Shape<D>::NC, 0, s>>>(
+                m, c, T(pc.inv_dt), T(m.hi - m.lo), Uo, Un, x, out, mm->d_flags, mm->d_elist + c0, cnt);
+            chns_count_launches(1);
+        }
+    } else {
+        const int64_t blocks = (m.E + EPB - 1) / EPB;
+        if (mm->scatter == SCAT_WARPAGG)
+            elem_rj_kernel<D, T, MODE, SCAT_WARPAGG><<<(unsigned)blocks, EPB * Shape<D>::NC, 0, s>>>(
+                m, c, T(pc.inv_dt), T(m.hi - m.lo), Uo, Un, x, out, mm->d_flags, nullptr, m.E);
+        else
+            elem_rj_kernel<D, T, MODE, SCAT_ATOMIC><<<(unsigned)blocks, EPB * Shape<D>::NC, 0, s>>>(
+                m, c, T(pc.inv_dt), T(m.hi - m.lo), Uo, Un, x, out, mm->d_flags, nullptr, m.E);
+        chns_count_launches(1);
+    }
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     const int64_t nb = m.NB > 0 ? m.NB : 1;
@@ -809,18 +912,31 @@ cudaError_t launch_vjp(const chns_mesh* mm, const PhysConst& pc, const double* U
     if (err == cudaSuccess && gCn) err = cudaMemsetAsync(gCn, 0, sizeof(double), s);
     if (err != cudaSuccess) return err;
     const int64_t nb = m.NB > 0 ? m.NB : 1;
-    if (m.dim == 2) {
-        const int EPB = 64 / 4;
-        { elem_vjp_kernel<2><<<(unsigned)((m.E + EPB - 1) / EPB), 64, 0, s>>>( m, make_pcst<double>(pc), pc.Cn, pc.inv_dt, U_old, U_lin, w, gU_new, gU_old, gCn, pin); chns_count_launches(1); }
-        err = cudaGetLastError();
-        if (err != cudaSuccess) return err;
+    const PCst<double> c = make_pcst<double>(pc);
+    auto elems = [&](auto dimtag) {
+        constexpr int D = decltype(dimtag)::value;
+        constexpr int EPB = 64 / (1 << D);
+        if (mm->scatter == SCAT_PLAIN) {
+            for (size_t k = 0; k + 1 < mm->colour_off.size(); ++k) {
+                const int64_t c0 = mm->colour_off[k], cnt = mm->colour_off[k + 1] - c0;
+                if (cnt <= 0) continue;
+                elem_vjp_kernel<D, SCAT_PLAIN><<<(unsigned)((cnt + EPB - 1) / EPB), 64, 0, s>>>(
+                    m, c, pc.Cn, pc.inv_dt, U_old, U_lin, w, gU_new, gU_old, gCn, pin, mm->d_elist + c0, cnt);
+                chns_count_launches(1);
+            }
+        } else {
+            elem_vjp_kernel<D, SCAT_ATOMIC><<<(unsigned)((m.E + EPB - 1) / EPB), 64, 0, s>>>(
+                m, c, pc.Cn, pc.inv_dt, U_old, U_lin, w, gU_new, gU_old, gCn, pin, nullptr, m.E);
+            chns_count_launches(1);
+        }
+    };
+    if (m.dim == 2) elems(std::integral_constant<int, 2>());
+    else elems(std::integral_constant<int, 3>());
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    if (m.dim == 2)
         { bc_vjp_kernel<2><<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(m, w, gU_new, gU_old, pin); chns_count_launches(1); }
-    } else {
-        const int EPB = 64 / 8;
-        { elem_vjp_kernel<3><<<(unsigned)((m.E + EPB - 1) / EPB), 64, 0, s>>>( m, make_pcst<double>(pc), pc.Cn, pc.inv_dt, U_old, U_lin, w, gU_new, gU_old, gCn, pin); chns_count_launches(1); }
-        err = cudaGetLastError();
-        if (err != cudaSuccess) return err;
+    else
         { bc_vjp_kernel<3><<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(m, w, gU_new, gU_old, pin); chns_count_launches(1); }
-    }
     return cudaGetLastError();
 }

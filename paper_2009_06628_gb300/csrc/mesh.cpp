@@ -322,6 +322,7 @@ extern "C" void chns_mesh_destroy(chns_mesh* m) {
     cudaFree(m->d_nflag);
     cudaFree(m->d_bnodes);
     cudaFree(m->d_bcval);
+    cudaFree(m->d_elist);
     cudaFree(m->d_anchor);
     cudaFree(m->d_nmass);
     cudaFree(m->d_partials);
@@ -386,4 +387,91 @@ extern "C" chns_status chns_mesh_set_velocity_bc(chns_mesh* m, const uint8_t* fa
         // coarse multigrid levels keep the pressure operator only; nothing to update
     }
     return CHNS_OK;
+}
+
+// Greedy element colouring for the deterministic scatter: two elements that share an
+// independent node (a corner, or a constraint parent of a hanging corner) get different
+// colours.  Elements are visited in Morton order and take the smallest colour not used by
+// an already coloured element sharing one of their nodes; within a colour the Morton
+// order is kept.
+static chns_status build_colouring(chns_mesh* m) {
+    const int64_t E = m->dm.E, N = m->dm.N;
+    const int nc = m->dm.nc;
+    auto nodes_of = [&](int64_t e, int32_t* out) -> int {
+        int k = 0;
+        for (int a = 0; a < nc; ++a) {
+            const int32_t ent = m->h_e2n[(size_t)e * nc + a];
+            if (ent >= 0) {
+                out[k++] = ent;
+            } else {
+                const int32_t* hp = &m->h_hang[(size_t)(-ent - 1) * 4];
+                const int np = hp[2] < 0 ? 2 : 4;
+                for (int j = 0; j < np; ++j) out[k++] = hp[j];
+            }
+        }
+        return k;
+    };
+    std::vector<int64_t> off((size_t)N + 1, 0);
+    int32_t buf[32];
+    for (int64_t e = 0; e < E; ++e) {
+        const int k = nodes_of(e, buf);
+        for (int i = 0; i < k; ++i) off[(size_t)buf[i] + 1]++;
+    }
+    for (int64_t n = 0; n < N; ++n) off[(size_t)n + 1] += off[(size_t)n];
+    std::vector<int32_t> adj((size_t)off[(size_t)N]);
+    {
+        std::vector<int64_t> pos(off.begin(), off.end() - 1);
+        for (int64_t e = 0; e < E; ++e) {
+            const int k = nodes_of(e, buf);
+            for (int i = 0; i < k; ++i) adj[(size_t)pos[(size_t)buf[i]]++] = (int32_t)e;
+        }
+    }
+    std::vector<int8_t> colour((size_t)E, -1);
+    int ncol = 0;
+    for (int64_t e = 0; e < E; ++e) {
+        uint64_t used = 0;
+        const int k = nodes_of(e, buf);
+        for (int i = 0; i < k; ++i)
+            for (int64_t j = off[(size_t)buf[i]]; j < off[(size_t)buf[i] + 1]; ++j) {
+                const int8_t c = colour[(size_t)adj[(size_t)j]];
+                if (c >= 0) used |= 1ull << c;
+            }
+        int c = 0;
+        while (c < 64 && ((used >> c) & 1ull)) ++c;
+        if (c >= 64) { chns_set_error("element colouring needs more than 64 colours"); return CHNS_EINVAL; }
+        colour[(size_t)e] = (int8_t)c;
+        ncol = std::max(ncol, c + 1);
+    }
+    std::vector<int64_t> coff((size_t)ncol + 1, 0);
+    for (int64_t e = 0; e < E; ++e) coff[(size_t)colour[(size_t)e] + 1]++;
+    for (int c = 0; c < ncol; ++c) coff[(size_t)c + 1] += coff[(size_t)c];
+    std::vector<int32_t> elist((size_t)E);
+    {
+        std::vector<int64_t> pos(coff.begin(), coff.end() - 1);
+        for (int64_t e = 0; e < E; ++e) elist[(size_t)pos[(size_t)colour[(size_t)e]]++] = (int32_t)e;
+    }
+    int32_t* d = nullptr;
+    chns_status st = dev_upload(&d, elist);
+    if (st != CHNS_OK) return st;
+    cudaFree(m->d_elist);
+    m->d_elist = d;
+    m->colour_off = coff;
+    return CHNS_OK;
+}
+
+extern "C" chns_status chns_mesh_set_scatter(chns_mesh* m, int32_t mode) {
+    if (!m || mode < 0 || mode > 2) {
+        chns_set_error("chns_mesh_set_scatter: mode must be 0 (atomics), 1 (colouring) or 2 (warp-aggregated)");
+        return CHNS_EINVAL;
+    }
+    if (mode == 1 && m->colour_off.empty()) {
+        chns_status st = build_colouring(m);
+        if (st != CHNS_OK) return st;
+    }
+    m->scatter = mode;
+    return CHNS_OK;
+}
+
+extern "C" int32_t chns_mesh_num_colours(const chns_mesh* m) {
+    return (m && !m->colour_off.empty()) ? (int32_t)m->colour_off.size() - 1 : 0;
 }
