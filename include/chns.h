@@ -141,6 +141,19 @@ typedef struct {
 chns_status chns_mesh_create(int32_t dim, int32_t max_level, int64_t n_leaves,
                              const chns_leaf* leaves, double lo, double hi, chns_mesh** out);
 
+/* Triquadratic (Q2) elements (Section 5.1 uses quadratic elements; NEXT-4) on the uniform
+ * octree of one level: 3^d nodes per element on the lattice of half the element size, the
+ * 3-point Gauss rule per axis, no hanging nodes.  Elements are in Morton order of their
+ * anchors; nodes in Morton order of their integer coordinates, which are in units of
+ * 2^-(level + 1) (chns_mesh_node_coords; the mesh's coordinate level is level + 1).  Element
+ * node a = a_0 + 3 a_1 (+ 9 a_2) sits at 2 * anchor + a_k along axis k.  A Q2 mesh serves
+ * chns_residual, chns_jvp (FP64 and FP32), chns_vjp and chns_mesh_set_velocity_bc; the
+ * strong residuals then include the pure second derivatives (the full Hessian of phi, the
+ * Laplacians of v and mu) that vanish on Q1.  Other calls return CHNS_EINVAL for it, and so
+ * does pin_pressure = 1.  Limits: 1 <= level <= 8 (3D) or 11 (2D). */
+chns_status chns_mesh_create_q2(int32_t dim, int32_t level, double lo, double hi, chns_mesh** out);
+int32_t chns_mesh_order(const chns_mesh* mesh);   /* 1 (Q1) or 2 (Q2); -1 for NULL */
+
 /* Free a mesh and its device memory (NULL is ignored). */
 void chns_mesh_destroy(chns_mesh* mesh);
 

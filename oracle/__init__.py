@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU-baseline
 and reference legs of the benchmark may import it; the library never does.
 """
-from .mesh import Mesh
-from .chns import Oracle, Params, basis_tables
+from .mesh import Mesh, MeshQ2
+from .chns import Oracle, Params, basis_tables, basis_tables_q2
 
-__all__ = ["Mesh", "Oracle", "Params", "basis_tables"]
+__all__ = ["Mesh", "MeshQ2", "Oracle", "Params", "basis_tables", "basis_tables_q2"]

@@ -96,6 +96,42 @@ def basis_tables(dim):
     return torch.tensor(N, dtype=DT), torch.tensor(dN, dtype=DT), torch.tensor(d2N, dtype=DT), xq
 
 
+def basis_tables_q2(dim):
+    """Q2 (tensor-product quadratic Lagrange) basis on [-1,1]^d at the 3^d Gauss points
+    (0, +-sqrt(3/5); weights 8/9, 5/9).  Node a = a_0 + 3 a_1 (+ 9 a_2) sits at
+    xi_k = a_k - 1; Gauss point q likewise.  1D: L_0 = xi(xi-1)/2, L_1 = 1 - xi^2,
+    L_2 = xi(xi+1)/2.  Returns N[q,a], dN[q,a,k], d2N[q,a,k,l], the points (q, d) and the
+    weights w_q (product of the 1D weights)."""
+    g = math.sqrt(0.6)
+    pts1 = np.array([-g, 0.0, g])
+    w1 = np.array([5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0])
+    L = lambda j, t: (t * (t - 1.0) / 2.0, 1.0 - t * t, t * (t + 1.0) / 2.0)[j]
+    dL = lambda j, t: (t - 0.5, -2.0 * t, t + 0.5)[j]
+    d2L = lambda j, t: (1.0, -2.0, 1.0)[j]
+    n = 3 ** dim
+    idx = np.array([[(a // 3 ** k) % 3 for k in range(dim)] for a in range(n)])
+    N = np.zeros((n, n))
+    dN = np.zeros((n, n, dim))
+    d2N = np.zeros((n, n, dim, dim))
+    xq = pts1[idx]                                      # (q, d)
+    wq = np.prod(w1[idx], axis=1)
+    for q in range(n):
+        t = xq[q]
+        for a in range(n):
+            f = [L(idx[a, k], t[k]) for k in range(dim)]
+            df = [dL(idx[a, k], t[k]) for k in range(dim)]
+            N[q, a] = np.prod(f)
+            for k in range(dim):
+                dN[q, a, k] = df[k] * np.prod([f[j] for j in range(dim) if j != k])
+                for l in range(dim):
+                    if l == k:
+                        d2N[q, a, k, k] = d2L(idx[a, k], t[k]) * np.prod([f[j] for j in range(dim) if j != k])
+                    else:
+                        d2N[q, a, k, l] = df[k] * df[l] * np.prod([f[j] for j in range(dim) if j not in (k, l)])
+    return (torch.tensor(N, dtype=DT), torch.tensor(dN, dtype=DT), torch.tensor(d2N, dtype=DT), xq,
+            torch.tensor(wq, dtype=DT))
+
+
 class Params:
     """Physical and numerical parameters of one time step."""
 
@@ -129,7 +165,12 @@ class Oracle:
         self.m = mesh
         d = mesh.dim
         self.d, self.nc, self.nf = d, mesh.nc, mesh.nf
-        self.N, self.dN, self.d2N, self.xq_ref = basis_tables(d)
+        self.order = getattr(mesh, "order", 1)
+        if self.order == 2:
+            self.N, self.dN, self.d2N, self.xq_ref, self.wq = basis_tables_q2(d)
+        else:
+            self.N, self.dN, self.d2N, self.xq_ref = basis_tables(d)
+            self.wq = None                                # unit Gauss weights
         sel = slice(None) if elements is None else np.asarray(elements)
         self.P = torch.tensor(mesh.parents[sel], dtype=torch.int64)
         self.W = torch.tensor(mesh.weights[sel], dtype=DT)
@@ -157,9 +198,17 @@ class Oracle:
         self.xq = torch.einsum("qa,ead->eqd", self.N, cx)
         self.detJ = (0.5 * self.h) ** d           # times unit Gauss weights
         # integral of each independent node's basis function (hanging weights included)
-        loc = self.N.sum(0).reshape(1, -1) * self.detJ.reshape(-1, 1)        # (E, nc)
+        loc = self._wq(self.N).sum(0).reshape(1, -1) * self.detJ.reshape(-1, 1)        # (E, nc)
         self.node_mass = self.scatter(loc, mesh.N)
         self.volume = (mesh.hi - mesh.lo) ** d
+
+    def _wq(self, a, axis=0):
+        """a times the Gauss weights along its Gauss-point axis (Q1: unit weights, a unchanged)."""
+        if self.wq is None:
+            return a
+        shape = [1] * a.dim()
+        shape[axis] = -1
+        return a * self.wq.reshape(shape)
 
     # -- gather / scatter with hanging-node constraints (Section 4) -------------
     def gather(self, U):
@@ -313,6 +362,7 @@ class Oracle:
 
         # test-function contraction: N_a f0 + dN_a/dx . f1, times |det J| w_q
         dNx = self.dN.unsqueeze(0) * (2.0 / self.h).reshape(-1, 1, 1, 1)    # (E,q,a,k)
+        f0, f1 = self._wq(f0, 1), self._wq(f1, 1)
         r_loc = (torch.einsum("qa,eqf->eaf", self.N, f0)
                  + torch.einsum("eqak,eqfk->eaf", dNx, f1)) * self.detJ.reshape(-1, 1, 1)
         R = self.scatter(r_loc, U_new.shape[0])
@@ -453,7 +503,7 @@ class Oracle:
         """Integral of phi over the domain."""
         phi_l = self.gather(U[:, self.d + 1])
         val, _, _ = self.interp(phi_l)
-        return float((val * self.detJ.reshape(-1, 1)).sum())
+        return float((self._wq(val, 1) * self.detJ.reshape(-1, 1)).sum())
 
     def energy(self, prm, U, Cn=None):
         """(kinetic, free, gravitational) parts of E_tot (Eq. energy_functional):
@@ -466,7 +516,7 @@ class Oracle:
         val, grad, _ = self.interp(ul)
         ps, _, _ = self.interp(self.gather(torch.clamp(U[:, d + 1], -1.0, 1.0)))
         rho = prm.alpha * ps + prm.beta
-        w = self.detJ.reshape(-1, 1)
+        w = self._wq(self.detJ.reshape(-1, 1).expand(-1, self.N.shape[0]), 1)
         v = val[..., :d]
         phi = val[..., d + 1]
         gphi = grad[..., d + 1, :]
@@ -478,7 +528,7 @@ class Oracle:
 
     def mass_matrix(self):
         """Consistent Q1 mass matrix on independent nodes (scipy CSR)."""
-        Me = torch.einsum("qa,qb->ab", self.N, self.N)                   # reference
+        Me = torch.einsum("qa,qb->ab", self._wq(self.N), self.N)          # reference
         rows, cols, vals = [], [], []
         P = self.m.parents
         W = self.m.weights
@@ -503,7 +553,7 @@ class Oracle:
         pl = self.gather(phi)
         val, grad, _ = self.interp(pl)
         dNx = self.dN.unsqueeze(0) * (2.0 / self.h).reshape(-1, 1, 1, 1)
-        w = self.detJ.reshape(-1, 1)
+        w = self._wq(self.detJ.reshape(-1, 1).expand(-1, self.N.shape[0]), 1)
         r = (torch.einsum("qa,eq->ea", self.N, (val ** 3 - val) * w)
              + torch.einsum("eqak,eqk->ea", dNx, Cn ** 2 * grad * w.unsqueeze(-1)))
         return self.scatter(r, phi.shape[0])

@@ -180,3 +180,50 @@ class Mesh:
         flags[near & (self.level < max_level)] = 1
         flags[~near & (self.level > min_level)] = -1
         return flags
+
+
+class MeshQ2:
+    """Triquadratic (Q2) elements on a uniform octree of one level (no hanging nodes):
+    3^d nodes per element on the lattice of half the element size.  Node coordinates are
+    integers in units of 2^-(level + 1); independent nodes are numbered in Morton order of
+    those coordinates.  Element node a = a_0 + 3 a_1 (+ 9 a_2), a_k in {0, 1, 2}, sits at
+    2 * anchor + a_k along axis k.  Exposes the attributes of ``Mesh`` that the oracle
+    uses; every node is independent (weights 1 in slot 0)."""
+
+    order = 2
+
+    def __init__(self, dim, level, lo=0.0, hi=1.0):
+        d = self.dim = int(dim)
+        L = self.max_level = int(level)
+        self.lo, self.hi = float(lo), float(hi)
+        self.nc = 3 ** d
+        self.nf = d + 3
+        n = 1 << L
+        grids = np.meshgrid(*[np.arange(n)] * d, indexing="ij")
+        anchors = np.stack([g.reshape(-1) for g in grids], axis=1)           # units of 2^-L
+        order = np.argsort(_morton(anchors, L))
+        self.anchors = anchors[order]
+        self.E = anchors.shape[0]
+        self.level = np.full(self.E, L, dtype=np.int64)
+        self.size = np.ones(self.E, dtype=np.int64)
+        self.h = (self.hi - self.lo) * np.full(self.E, 0.5 ** L)
+        loc = np.array([[(a // 3 ** k) % 3 for k in range(d)] for a in range(self.nc)], dtype=np.int64)
+        pts = 2 * self.anchors[:, None, :] + loc[None, :, :]                  # units of 2^-(L+1)
+        keys_all = _morton(pts.reshape(-1, d), L + 2)
+        keys = np.unique(keys_all)
+        self.N = keys.shape[0]
+        nodes = np.zeros((self.N, d), dtype=np.int64)
+        for b in range(L + 2):
+            for k in range(d):
+                nodes[:, k] |= ((keys >> (b * d + k)) & 1) << b
+        self.nodes = nodes
+        side = 2 * n
+        self.x = self.lo + (self.hi - self.lo) * nodes.astype(np.float64) / float(side)
+        self.boundary = np.any((nodes == 0) | (nodes == side), axis=1)
+        idx = np.searchsorted(keys, keys_all).reshape(self.E, self.nc)
+        self.parents = np.zeros((self.E, self.nc, 4), dtype=np.int64)
+        self.parents[:, :, 0] = idx
+        self.weights = np.zeros((self.E, self.nc, 4))
+        self.weights[:, :, 0] = 1.0
+        self.hanging = np.zeros((self.E, self.nc), dtype=bool)
+        self.corner_x = self.lo + (self.hi - self.lo) * pts.astype(np.float64) / float(side)

@@ -75,6 +75,9 @@ SIGNATURES = [
     ("chns_mesh_create", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, P, ctypes.c_double,
                                         ctypes.c_double, ctypes.POINTER(ctypes.c_void_p)]),
     ("chns_mesh_destroy", None, [P]),
+    ("chns_mesh_create_q2", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                           ctypes.POINTER(ctypes.c_void_p)]),
+    ("chns_mesh_order", ctypes.c_int32, [P]),
     ("chns_mesh_num_nodes", ctypes.c_int64, [P]),
     ("chns_mesh_num_elements", ctypes.c_int64, [P]),
     ("chns_mesh_num_hanging", ctypes.c_int64, [P]),
@@ -399,3 +402,23 @@ def adapt(mesh, U, phi_threshold, min_level, max_level):
     new = Mesh(mesh.dim, L, leaves, mesh.lo, mesh.hi)
     T = Transfer(mesh, new)
     return new, T.apply(U), fl
+
+
+class MeshQ2(Mesh):
+    """Owns a Q2 chns_mesh on the uniform octree of one level (node coordinates in units of
+    2^-(level + 1))."""
+
+    def __init__(self, dim, level, lo=0.0, hi=1.0):
+        L = load()
+        h = ctypes.c_void_p()
+        _check(L.chns_mesh_create_q2(int(dim), int(level), float(lo), float(hi), ctypes.byref(h)))
+        self._h = h
+        self.leaves = None
+        self.dim = int(dim)
+        self.nf = self.dim + 3
+        self.level = int(level)
+        self.max_level = int(level) + 1       # resolution of the node coordinates
+        self.lo, self.hi = float(lo), float(hi)
+        self.N = int(L.chns_mesh_num_nodes(h))
+        self.E = int(L.chns_mesh_num_elements(h))
+        self.H = 0

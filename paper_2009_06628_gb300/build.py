@@ -9,7 +9,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libchns.so")
-SOURCES = ["mesh.cpp", "capi.cpp", "element_kernels.cu", "reduce_kernels.cu", "solver.cu", "mass_static.cu", "objective.cu", "peaks.cu", "multigrid.cu", "adapt.cu"]
+SOURCES = ["mesh.cpp", "capi.cpp", "element_kernels.cu", "reduce_kernels.cu", "solver.cu", "mass_static.cu", "objective.cu", "peaks.cu", "multigrid.cu", "adapt.cu", "q2_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fopenmp",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

@@ -64,6 +64,7 @@ extern "C" chns_status chns_adapt_flags(const chns_mesh* m, const double* U, dou
         chns_set_error("chns_adapt_flags: bad argument (threshold > 0, 0 <= min_level <= max_level <= 20)");
         return CHNS_EINVAL;
     }
+    if (chns_require_q1(m, "chns_adapt_flags") != CHNS_OK) return CHNS_EINVAL;
     const int g = (int)((m->dm.E + 255) / 256);
     adapt_flags_kernel<<<g, 256, 0, (cudaStream_t)stream>>>(m->dm, U, phi_threshold, min_level, max_level, flags);
     chns_count_launches(1);

@@ -33,6 +33,14 @@ int chns_num_sms() {
     return sms;
 }
 
+chns_status chns_require_q1(const chns_mesh* m, const char* what) {
+    if (m && m->order != 1) {
+        chns_set_error(std::string(what) + " is available for Q1 meshes only (Q2 meshes: residual, J x, J^T w)");
+        return CHNS_EINVAL;
+    }
+    return CHNS_OK;
+}
+
 chns_status chns_check_rows(const chns_mesh* m, const void* p, int elem_bytes) {
     // 3D node rows (6 values) are read as pairs: the vector must start on 2 * elem_bytes
     if (m && m->dm.dim == 3 && p && ((uintptr_t)p % (uintptr_t)(2 * elem_bytes)) != 0) {
@@ -87,6 +95,11 @@ extern "C" chns_status chns_residual(const chns_mesh* m, const chns_params* p, c
     if (st != CHNS_OK) return st;
     if (!U_old || !U_new || !R) { chns_set_error("null vector"); return CHNS_EINVAL; }
     if ((st = chns_check_rows(m, U_old, 8)) != CHNS_OK || (st = chns_check_rows(m, U_new, 8)) != CHNS_OK) return st;
+    if (m->order == 2) {
+        if (p->pin_pressure == 1) { chns_set_error("Q2 meshes take pin_pressure 0 or 2"); return CHNS_EINVAL; }
+        CHNS_CUDA(q2_launch_residual(m, pc, U_old, U_new, R, (cudaStream_t)stream));
+        return CHNS_OK;
+    }
     CHNS_CUDA(launch_residual(m, pc, U_old, U_new, R, p->pin_pressure, (cudaStream_t)stream));
     return CHNS_OK;
 }
@@ -104,6 +117,14 @@ extern "C" chns_status chns_jvp(const chns_mesh* m, const chns_params* p, const 
             return st;
     }
     cudaStream_t s = (cudaStream_t)stream;
+    if (m->order == 2 && (precision == 0 || precision == 1)) {
+        if (p->pin_pressure == 1) { chns_set_error("Q2 meshes take pin_pressure 0 or 2"); return CHNS_EINVAL; }
+        if (precision == 0)
+            CHNS_CUDA(q2_launch_jvp64(m, pc, (const double*)U_old, (const double*)U_lin, (const double*)x, (double*)y, s));
+        else
+            CHNS_CUDA(q2_launch_jvp32(m, pc, (const float*)U_old, (const float*)U_lin, (const float*)x, (float*)y, s));
+        return CHNS_OK;
+    }
     if (precision == 0) {
         CHNS_CUDA(launch_jvp64(m, pc, (const double*)U_old, (const double*)U_lin, (const double*)x, (double*)y,
                                p->pin_pressure, s));
@@ -124,12 +145,18 @@ extern "C" chns_status chns_vjp(const chns_mesh* m, const chns_params* p, const 
     if (st != CHNS_OK) return st;
     if (!U_old || !U_lin || !w || !gU_new) { chns_set_error("null vector"); return CHNS_EINVAL; }
     if ((st = chns_check_rows(m, U_old, 8)) != CHNS_OK || (st = chns_check_rows(m, U_lin, 8)) != CHNS_OK) return st;
+    if (m->order == 2) {
+        if (p->pin_pressure == 1) { chns_set_error("Q2 meshes take pin_pressure 0 or 2"); return CHNS_EINVAL; }
+        CHNS_CUDA(q2_launch_vjp(m, pc, U_old, U_lin, w, gU_new, gU_old, gCn, (cudaStream_t)stream));
+        return CHNS_OK;
+    }
     CHNS_CUDA(launch_vjp(m, pc, U_old, U_lin, w, gU_new, gU_old, gCn, p->pin_pressure, (cudaStream_t)stream));
     return CHNS_OK;
 }
 
 extern "C" chns_status chns_mass(const chns_mesh* m, const double* U, double* out, void* stream) {
     if (!m || !U || !out) { chns_set_error("null argument"); return CHNS_EINVAL; }
+    if (chns_require_q1(m, "chns_mass") != CHNS_OK) return CHNS_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     CHNS_CUDA(launch_mass(m, U, m->d_partials + (size_t)m->n_partials * 8 - 8, s));
     CHNS_CUDA(cudaMemcpyAsync(m->h_pinned, m->d_partials + (size_t)m->n_partials * 8 - 8, sizeof(double),
@@ -145,6 +172,7 @@ extern "C" chns_status chns_energy(const chns_mesh* m, const chns_params* p, con
     chns_status st = chns_check_params(m, p, &pc);
     if (st != CHNS_OK) return st;
     if (!U || !out) { chns_set_error("null argument"); return CHNS_EINVAL; }
+    if ((st = chns_require_q1(m, "chns_energy")) != CHNS_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     double* dev_out = m->d_partials + (size_t)m->n_partials * 8 - 8;
     CHNS_CUDA(launch_energy(m, pc, U, dev_out, s));

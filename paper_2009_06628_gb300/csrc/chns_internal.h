@@ -30,6 +30,8 @@ struct MGHier;    // geometric multigrid hierarchy of the pressure Schur Laplaci
 struct chns_mesh {
     DevMesh dm;
     int32_t max_level;
+    int32_t order = 1;                 // 1: Q1 on a 2:1 octree; 2: Q2 on a uniform octree
+    int32_t q2_level = 0;              // Q2: the element level (max_level = q2_level + 1 then)
     int32_t device = 0;                // CUDA device ordinal that holds the mesh's arrays
     std::vector<int32_t> node_coords;  // host copy, N * dim
     // host copies of the element arrays (transfer operators, coarse meshes, remeshing)
@@ -159,6 +161,18 @@ struct MGHier {
 };
 chns_status mg_hier_build(chns_mesh* m);   // no-op when m->mg exists
 void chns_mg_free(MGHier* mg);
+
+// Q2 element kernels (q2_kernels.cu)
+cudaError_t q2_launch_residual(const chns_mesh* m, const PhysConst& pc, const double* Uo, const double* Un, double* R,
+                               cudaStream_t s);
+cudaError_t q2_launch_jvp64(const chns_mesh* m, const PhysConst& pc, const double* Uo, const double* Un,
+                            const double* x, double* y, cudaStream_t s);
+cudaError_t q2_launch_jvp32(const chns_mesh* m, const PhysConst& pc, const float* Uo, const float* Un, const float* x,
+                            float* y, cudaStream_t s);
+cudaError_t q2_launch_vjp(const chns_mesh* m, const PhysConst& pc, const double* Uo, const double* Un,
+                          const double* w, double* gn, double* go, double* gCn, cudaStream_t s);
+// CHNS_EINVAL (naming `what`) unless the mesh has Q1 elements
+chns_status chns_require_q1(const chns_mesh* m, const char* what);
 
 // launch accounting (capi.cpp)
 void chns_count_launches(int n);

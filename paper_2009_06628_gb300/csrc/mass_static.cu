@@ -121,6 +121,7 @@ extern "C" chns_status chns_mass_static(const chns_mesh* m, const double* U, dou
         chns_set_error("chns_mass_static: null argument");
         return CHNS_EINVAL;
     }
+    if (chns_require_q1(m, "chns_mass_static") != CHNS_OK) return CHNS_EINVAL;
     if (m->dm.E > MS_MAX_ELEMENTS) {
         chns_set_error("chns_mass_static: the mesh has more than 67,108,864 elements (the static scratch "
                        "holds 16,384 block sums of 4,096 elements); use chns_mass");

@@ -6,6 +6,7 @@
 #include <parallel/algorithm>
 #include <cstring>
 #include <new>
+#include <utility>
 
 #include "chns_internal.h"
 #include "morton.h"
@@ -464,6 +465,7 @@ extern "C" chns_status chns_mesh_set_scatter(chns_mesh* m, int32_t mode) {
         chns_set_error("chns_mesh_set_scatter: mode must be 0 (atomics), 1 (colouring) or 2 (warp-aggregated)");
         return CHNS_EINVAL;
     }
+    if (mode != 0 && chns_require_q1(m, "scatter modes 1 and 2") != CHNS_OK) return CHNS_EINVAL;
     if (mode == 1 && m->colour_off.empty()) {
         chns_status st = build_colouring(m);
         if (st != CHNS_OK) return st;
@@ -475,3 +477,125 @@ extern "C" chns_status chns_mesh_set_scatter(chns_mesh* m, int32_t mode) {
 extern "C" int32_t chns_mesh_num_colours(const chns_mesh* m) {
     return (m && !m->colour_off.empty()) ? (int32_t)m->colour_off.size() - 1 : 0;
 }
+
+// Q2 mesh of a uniform octree at `level`: elements in Morton order of their anchors, 3^d
+// nodes each on the lattice of half the element size, numbered in Morton order of their
+// integer coordinates (units of 2^-(level + 1)); no hanging nodes.
+extern "C" chns_status chns_mesh_create_q2(int32_t dim, int32_t level, double lo, double hi, chns_mesh** out) {
+    chns_set_error("");
+    if (!out) { chns_set_error("null argument"); return CHNS_EINVAL; }
+    *out = nullptr;
+    if (dim != 2 && dim != 3) { chns_set_error("dim must be 2 or 3"); return CHNS_EINVAL; }
+    if (level < 1 || level > (dim == 3 ? 8 : 11)) {
+        chns_set_error("Q2 level must be in [1, 8] (3D) or [1, 11] (2D)");
+        return CHNS_EINVAL;
+    }
+    if (!(hi > lo)) { chns_set_error("domain must satisfy hi > lo"); return CHNS_EINVAL; }
+    const int d = dim, L = level, NN = d == 2 ? 9 : 27;
+    const int64_t n = (int64_t)1 << L, E = d == 2 ? n * n : n * n * n;
+    const int64_t side = 2 * n;
+    std::vector<std::pair<uint64_t, int64_t>> ek((size_t)E);
+    for (int64_t i = 0; i < E; ++i) {
+        int64_t a[3] = {i % n, (i / n) % n, d == 3 ? i / (n * n) : 0};
+        ek[(size_t)i] = {morton(d, a), i};
+    }
+    std::sort(ek.begin(), ek.end());
+    std::vector<int32_t> anchor((size_t)E * d);
+    std::vector<uint64_t> nkeys;
+    nkeys.reserve((size_t)E * NN);
+    for (int64_t e = 0; e < E; ++e) {
+        const int64_t i = ek[(size_t)e].second;
+        const int64_t a[3] = {i % n, (i / n) % n, d == 3 ? i / (n * n) : 0};
+        for (int k = 0; k < d; ++k) anchor[(size_t)e * d + k] = (int32_t)a[k];
+        for (int c = 0; c < NN; ++c) {
+            int64_t p[3] = {0, 0, 0};
+            for (int k = 0, cc = c; k < d; ++k, cc /= 3) p[k] = 2 * a[k] + cc % 3;
+            nkeys.push_back(morton(d, p));
+        }
+    }
+    std::vector<uint64_t> keys(nkeys);
+    std::sort(keys.begin(), keys.end());
+    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    const int64_t N = (int64_t)keys.size();
+    std::vector<int32_t> e2n((size_t)E * NN);
+    for (size_t j = 0; j < nkeys.size(); ++j)
+        e2n[j] = (int32_t)(std::lower_bound(keys.begin(), keys.end(), nkeys[j]) - keys.begin());
+    chns_mesh* m = new (std::nothrow) chns_mesh();
+    if (!m) { chns_set_error("host allocation failed"); return CHNS_ENOMEM; }
+    m->order = 2;
+    m->q2_level = L;
+    m->max_level = L + 1;
+    m->node_coords.resize((size_t)N * d);
+    std::vector<uint8_t> nflag((size_t)N, 0);
+    std::vector<int32_t> bnodes;
+    for (int64_t i = 0; i < N; ++i) {
+        bool bnd = false;
+        for (int c = 0; c < d; ++c) {
+            int64_t v = 0;
+            for (int b = 0; b <= L + 1; ++b) v |= (int64_t)((keys[(size_t)i] >> (b * d + c)) & 1) << b;
+            m->node_coords[(size_t)i * d + c] = (int32_t)v;
+            if (v == 0 || v == side) bnd = true;
+        }
+        if (bnd) {
+            nflag[(size_t)i] = (uint8_t)((1u << d) - 1u);
+            bnodes.push_back((int32_t)i);
+        }
+    }
+    // node masses: int N_a = (h/2)^d prod_k (1/3, 4/3, 1/3)[a_k]
+    std::vector<double> nmass((size_t)N, 0.0);
+    const double h = std::ldexp(hi - lo, -L), w1[3] = {1.0 / 3.0, 4.0 / 3.0, 1.0 / 3.0};
+    const double jac = std::pow(0.5 * h, d);
+    for (int64_t e = 0; e < E; ++e)
+        for (int c = 0; c < NN; ++c) {
+            double w = jac;
+            for (int k = 0, cc = c; k < d; ++k, cc /= 3) w *= w1[cc % 3];
+            nmass[(size_t)e2n[(size_t)e * NN + c]] += w;
+        }
+    std::vector<int8_t> level8((size_t)E, (int8_t)L);
+    std::vector<int32_t> hang(4, -1);
+    {
+        cudaError_t de = cudaGetDevice(&m->device);
+        if (de != cudaSuccess) { chns_mesh_destroy(m); return chns_cuda_status(de, "cudaGetDevice"); }
+    }
+    chns_status st;
+    if ((st = dev_upload(&m->d_e2n, e2n)) != CHNS_OK || (st = dev_upload(&m->d_hang, hang)) != CHNS_OK ||
+        (st = dev_upload(&m->d_level, level8)) != CHNS_OK || (st = dev_upload(&m->d_nflag, nflag)) != CHNS_OK ||
+        (st = dev_upload(&m->d_bnodes, bnodes)) != CHNS_OK || (st = dev_upload(&m->d_anchor, anchor)) != CHNS_OK ||
+        (st = dev_upload(&m->d_nmass, nmass)) != CHNS_OK) {
+        chns_mesh_destroy(m);
+        return st;
+    }
+    m->n_partials = 4096;
+    cudaError_t ce = cudaMalloc((void**)&m->d_partials, (size_t)m->n_partials * 8 * sizeof(double));
+    if (ce == cudaSuccess) ce = cudaMalloc((void**)&m->d_flags, 64);
+    if (ce == cudaSuccess) ce = cudaMemset(m->d_flags, 0, 64);
+    if (ce == cudaSuccess) ce = cudaMallocHost((void**)&m->h_pinned, 64 * sizeof(double));
+    if (ce != cudaSuccess) { chns_mesh_destroy(m); return chns_cuda_status(ce, "cudaMalloc(mesh workspace)"); }
+    DevMesh& dm = m->dm;
+    dm.dim = d;
+    dm.nc = NN;
+    dm.nf = d + 3;
+    dm.E = E;
+    dm.N = N;
+    dm.H = 0;
+    dm.NB = (int64_t)bnodes.size();
+    dm.e2n = m->d_e2n;
+    dm.hang = m->d_hang;
+    dm.level = m->d_level;
+    dm.nflag = m->d_nflag;
+    dm.bnodes = m->d_bnodes;
+    dm.bcval = nullptr;
+    dm.anchor = m->d_anchor;
+    dm.max_level = L + 1;
+    dm.lo = lo;
+    dm.hi = hi;
+    m->volume = std::pow(hi - lo, d);
+    m->h_e2n = std::move(e2n);
+    m->h_hang = std::move(hang);
+    m->h_anchor = std::move(anchor);
+    m->h_level = std::move(level8);
+    *out = m;
+    return CHNS_OK;
+}
+
+extern "C" int32_t chns_mesh_order(const chns_mesh* m) { return m ? m->order : -1; }

@@ -352,6 +352,8 @@ extern "C" chns_status chns_transfer_create(const chns_mesh* src, const chns_mes
         return CHNS_EINVAL;
     }
     *out = nullptr;
+    if (chns_require_q1(src, "chns_transfer_create") != CHNS_OK || chns_require_q1(dst, "chns_transfer_create") != CHNS_OK)
+        return CHNS_EINVAL;
     chns_transfer* t = new (std::nothrow) chns_transfer();
     if (!t) {
         chns_set_error("host allocation failed");

@@ -131,6 +131,7 @@ int obj_blocks(int64_t E) {
 
 extern "C" chns_status chns_free_energy_grad(const chns_mesh* m, const chns_params* p, const double* U, double* g,
                                              double* dCn, void* stream) {
+    if (chns_require_q1(m, "chns_free_energy_grad") != CHNS_OK) return CHNS_EINVAL;
     PhysConst pc;
     chns_status st = chns_check_params(m, p, &pc);
     if (st != CHNS_OK) return st;
@@ -160,6 +161,7 @@ extern "C" chns_status chns_free_energy_grad(const chns_mesh* m, const chns_para
 
 extern "C" chns_status chns_mu_rhs_vjp(const chns_mesh* m, const chns_params* p, const double* U, const double* lam,
                                        double* g_phi, double* dCn, void* stream) {
+    if (chns_require_q1(m, "chns_mu_rhs_vjp") != CHNS_OK) return CHNS_EINVAL;
     PhysConst pc;
     chns_status st = chns_check_params(m, p, &pc);
     if (st != CHNS_OK) return st;

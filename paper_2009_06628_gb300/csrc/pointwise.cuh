@@ -68,6 +68,9 @@ template <int D, class S>
 struct QPIn {
     S v[D], gv[D][D], p, gp[D], phi, gphi[D], H[D == 2 ? 1 : 3], mu, gmu[D], vdt[D], phidt, divnew,
         ps, gps[D];
+    // second derivatives that vanish on Q1 and are read only by the Q2 instantiation:
+    // pure second derivatives of phi, Laplacians of the velocity components and of mu
+    S Hd[D], lapv[D], lapmu;
 };
 
 template <int D, class S>
@@ -87,7 +90,10 @@ struct PCst {
 
 // The pointwise map of Definition 2 (Crank-Nicolson substitution, Section 3.3 end).
 // g = 4/h^2: the metric G = g I of the axis-aligned element (tr G = D g, G:G = D g^2).
-template <int D, class S, class R>
+// Q2: the strong residuals also carry the terms with pure second derivatives (they vanish
+// on Q1): d_i phi d_ii phi + d_i phi lap phi in the capillary term, eta lap v_i in the
+// viscous term, lap mu in R_phi.
+template <int D, class S, class R, bool Q2 = false>
 __device__ __forceinline__ void pointwise(const QPIn<D, S>& X, const PCst<R>& c, R g,
                                           QPOut<D, S>& F) {
     const S rho = c.alpha * X.ps + c.beta;
@@ -120,6 +126,13 @@ __device__ __forceinline__ void pointwise(const QPIn<D, S>& X, const PCst<R>& c,
 #pragma unroll
         for (int j = 0; j < D; ++j)
             if (j != i) cap = cap + X.H[hidx(i, j)] * X.gphi[j];
+        if constexpr (Q2) {
+            S lapphi = X.Hd[0];
+#pragma unroll
+            for (int k = 1; k < D; ++k) lapphi = lapphi + X.Hd[k];
+            cap = cap + X.gphi[i] * (X.Hd[i] + lapphi);
+            vs = vs + eta * X.lapv[i];
+        }
         conv[i] = cv;
         Jgv[i] = jg;
         S r = rho * (X.vdt[i] + cv) + c.inv_Pe * jg + c.Cn_We * cap + c.inv_We * X.gp[i] - c.inv_Re * vs;
@@ -129,7 +142,8 @@ __device__ __forceinline__ void pointwise(const QPIn<D, S>& X, const PCst<R>& c,
     S vg = X.v[0] * X.gphi[0];
 #pragma unroll
     for (int k = 1; k < D; ++k) vg = vg + X.v[k] * X.gphi[k];
-    const S Rphi = X.phidt + X.phi * Rc + vg;
+    S Rphi = X.phidt + X.phi * Rc + vg;
+    if constexpr (Q2) Rphi = Rphi - c.inv_PeCn * X.lapmu;
     const S irho = recip(rho);
     const S er = c.inv_Re * (eta * irho);
     const S rad_m = c.four_over_dt2 + g * vv + (g * c.inv_Pe) * (vJ * irho) + (c.C_I * R(D) * g * g) * (er * er);
@@ -177,7 +191,7 @@ __device__ __forceinline__ void pointwise(const QPIn<D, S>& X, const PCst<R>& c,
 
 // Reverse mode of `pointwise` in FP64: given the output adjoint Fb, return the input
 // adjoint Xb and the adjoint of Cn (Cn enters through Jc, Cn/We, 1/(Pe Cn), Cn^2).
-template <int D>
+template <int D, bool Q2 = false>
 __device__ __forceinline__ void pointwise_adjoint(const QPIn<D, double>& X, const PCst<double>& c,
                                                   double Cn, double g, const QPOut<D, double>& Fb,
                                                   QPIn<D, double>& Xb, double& Cnb) {
@@ -185,7 +199,9 @@ __device__ __forceinline__ void pointwise_adjoint(const QPIn<D, double>& X, cons
     const double rho = c.alpha * X.ps + c.beta;
     const double eta = c.gamma * X.ps + c.xi;
     double J[D], conv[D], Jgv[D], Rm[D], cap[D], visc[D];
-    double vv = 0.0, vJ = 0.0, Rc = 0.0, vg = 0.0;
+    double vv = 0.0, vJ = 0.0, Rc = 0.0, vg = 0.0, lapphi = 0.0;
+    if (Q2)
+        for (int k = 0; k < D; ++k) lapphi += X.Hd[k];
     for (int k = 0; k < D; ++k) {
         J[k] = c.Jc * X.gmu[k];
         vv += X.v[k] * X.v[k];
@@ -201,6 +217,10 @@ __device__ __forceinline__ void pointwise_adjoint(const QPIn<D, double>& X, cons
             vs += c.gamma * X.gps[j] * X.gv[i][j];
             if (j != i) cp += X.H[hidx(i, j)] * X.gphi[j];
         }
+        if (Q2) {
+            cp += X.gphi[i] * (X.Hd[i] + lapphi);
+            vs += eta * X.lapv[i];
+        }
         conv[i] = cv;
         Jgv[i] = jg;
         visc[i] = vs;
@@ -208,7 +228,7 @@ __device__ __forceinline__ void pointwise_adjoint(const QPIn<D, double>& X, cons
         Rm[i] = rho * (X.vdt[i] + cv) + c.inv_Pe * jg + c.Cn_We * cp + c.inv_We * X.gp[i] - c.inv_Re * vs +
                 (i == D - 1 ? c.inv_Fr * rho : 0.0);
     }
-    const double Rphi = X.phidt + X.phi * Rc + vg;
+    const double Rphi = X.phidt + X.phi * Rc + vg - (Q2 ? c.inv_PeCn * X.lapmu : 0.0);
     const double irho = 1.0 / rho, irho2 = irho * irho;
     const double er = c.inv_Re * eta * irho;
     const double GG = double(D) * g * g;
@@ -230,7 +250,8 @@ __device__ __forceinline__ void pointwise_adjoint(const QPIn<D, double>& X, cons
         for (int j = 0; j < D; ++j) Xb.gv[k][j] = 0.0;
     }
     for (int k = 0; k < (D == 2 ? 1 : 3); ++k) Xb.H[k] = 0.0;
-    Xb.p = Xb.phi = Xb.mu = Xb.phidt = Xb.divnew = Xb.ps = 0.0;
+    for (int k = 0; k < D; ++k) Xb.Hd[k] = Xb.lapv[k] = 0.0;
+    Xb.p = Xb.phi = Xb.mu = Xb.phidt = Xb.divnew = Xb.ps = Xb.lapmu = 0.0;
     Cnb = 0.0;
     const double iCn = 1.0 / Cn;
     const double dJc = -c.Jc * iCn, dinvPeCn = -c.inv_PeCn * iCn, dCnWe = c.inv_We, dCn2 = 2.0 * Cn;
@@ -322,7 +343,11 @@ __device__ __forceinline__ void pointwise_adjoint(const QPIn<D, double>& X, cons
         etab += 2.0 * c.C_I * GG * er * irho * c.inv_Re * radmb;
         rhob -= 2.0 * c.C_I * GG * er * er * irho * radmb;
     }
-    // Rphi = phidt + phi Rc + v . gphi
+    // Rphi = phidt + phi Rc + v . gphi (- inv_PeCn lap mu on Q2)
+    if (Q2) {
+        Xb.lapmu -= c.inv_PeCn * Rphib;
+        Cnb -= dinvPeCn * X.lapmu * Rphib;
+    }
     Xb.phidt += Rphib;
     Xb.phi += Rc * Rphib;
     Rcb += X.phi * Rphib;
@@ -345,8 +370,19 @@ __device__ __forceinline__ void pointwise_adjoint(const QPIn<D, double>& X, cons
     }
     // Rc = tr grad v
     for (int k = 0; k < D; ++k) Xb.gv[k][k] += Rcb;
-    // visc_i = sum_k gamma gps_k gv_ik; cap_i = sum_{j != i} H_ij gphi_j;
-    // Jgv_i = sum_j J_j gv_ij; conv_i = sum_j v_j gv_ij
+    // visc_i = sum_k gamma gps_k gv_ik (+ eta lap v_i); cap_i = sum_{j != i} H_ij gphi_j
+    // (+ gphi_i (Hd_i + lap phi)); Jgv_i = sum_j J_j gv_ij; conv_i = sum_j v_j gv_ij
+    if (Q2) {
+        double lapb = 0.0;
+        for (int i = 0; i < D; ++i) {
+            etab += X.lapv[i] * viscb[i];
+            Xb.lapv[i] += eta * viscb[i];
+            Xb.gphi[i] += (X.Hd[i] + lapphi) * capb[i];
+            Xb.Hd[i] += X.gphi[i] * capb[i];
+            lapb += X.gphi[i] * capb[i];
+        }
+        for (int k = 0; k < D; ++k) Xb.Hd[k] += lapb;
+    }
     for (int i = 0; i < D; ++i) {
         for (int j = 0; j < D; ++j) {
             Xb.gps[j] += c.gamma * X.gv[i][j] * viscb[i];

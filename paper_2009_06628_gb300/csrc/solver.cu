@@ -1166,6 +1166,7 @@ int mg_vcycle(MGHier* mg, int l, const float* ce0, cudaStream_t st) {
 
 extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* p, const chns_solver_opts* o,
                                         const double* U_old, double* U, chns_stats* stats, void* stream) {
+    if (chns_require_q1(mc, "chns_newton_step") != CHNS_OK) return CHNS_EINVAL;
     chns_mesh* m = const_cast<chns_mesh*>(mc);
     PhysConst pc;
     chns_status st = chns_check_params(mc, p, &pc);
@@ -1747,6 +1748,7 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
 }
 
 extern "C" chns_status chns_initial_mu(const chns_mesh* mc, const chns_params* p, double* U, void* stream) {
+    if (chns_require_q1(mc, "chns_initial_mu") != CHNS_OK) return CHNS_EINVAL;
     chns_mesh* m = const_cast<chns_mesh*>(mc);
     PhysConst pc;
     chns_status st = chns_check_params(mc, p, &pc);
@@ -1869,6 +1871,7 @@ __global__ void field_axpy_mass_kernel(double* __restrict__ v, int NF, int f, in
 extern "C" chns_status chns_step_adjoint(const chns_mesh* mc, const chns_params* p, const chns_solver_opts* o,
                                          const double* U_old, const double* U_new, const double* g, double* lambda,
                                          double* gU_old, double* gCn, chns_stats* stats, void* stream) {
+    if (chns_require_q1(mc, "chns_step_adjoint") != CHNS_OK) return CHNS_EINVAL;
     chns_mesh* m = const_cast<chns_mesh*>(mc);
     PhysConst pc;
     chns_status st = chns_check_params(mc, p, &pc);
@@ -2023,6 +2026,7 @@ extern "C" chns_status chns_step_adjoint(const chns_mesh* mc, const chns_params*
 // Jacobi-preconditioned CG to a relative residual of 1e-14.  Used by the reverse mode
 // of mu^0 (M is symmetric, so its adjoint is the same solve).
 extern "C" chns_status chns_mass_solve(const chns_mesh* mc, const double* rhs, double* x, void* stream) {
+    if (chns_require_q1(mc, "chns_mass_solve") != CHNS_OK) return CHNS_EINVAL;
     chns_mesh* m = const_cast<chns_mesh*>(mc);
     if (!m || !rhs || !x) { chns_set_error("null argument"); return CHNS_EINVAL; }
     chns_status st = ensure_ws(m, m->ws ? m->ws->restart : 1);

@@ -24,17 +24,23 @@ import pytest
 import sympy
 
 import synth
-from oracle import Mesh, Oracle, Params
+from oracle import Mesh, MeshQ2, Oracle, Params
 
 
-def _monomials(X):
+def _monomials(X, order=1):
+    """Q1: the products of distinct coordinates (1, x, y, xy, ...), a basis of the Q1
+    space.  Q2: the monomials of total degree <= 2 (1, x, y, x^2, xy, y^2, ...), which Q2
+    elements reproduce exactly and which have non-zero pure and mixed second derivatives
+    (the full Q2 basis would only make the symbolic expressions longer)."""
     d = len(X)
     out = []
-    for s in range(1 << d):
+    for s in range((order + 1) ** d):
+        a = [(s // (order + 1) ** k) % (order + 1) for k in range(d)]
+        if order == 2 and sum(a) > 2:
+            continue
         m = sympy.Integer(1)
         for k in range(d):
-            if (s >> k) & 1:
-                m = m * X[k]
+            m = m * X[k] ** a[k]
         out.append(m)
     return out
 
@@ -47,17 +53,19 @@ def _physics(dim):
                 dt=0.02, C_I=6.0, C_phi=6.0, pin_pressure=0)
 
 
-def hand_rows(dim, level=2, seed=11):
+def hand_rows(dim, level=2, seed=11, order=1):
     """Returns (mesh, params, node, U_old, U_new, terms) where terms[row] is a dict
     {name: value} of the separate weak-form terms of that row of the interior node
     x_A = (1/2, ..., 1/2).  Every field is a multilinear polynomial plus a multiple of the
     hat function of x_A (itself multilinear on each element, so the field stays in the
     Q1 space, while its discrete Laplacian at x_A is not zero and the diffusion terms
-    are visible)."""
+    are visible).  order=2: Q2 elements (fields with squares of each coordinate, the
+    quadratic hat of the vertex node, the 3-point Gauss rule), where the strong residuals
+    also carry the pure second derivatives."""
     prm = _physics(dim)
     h = 1.0 / (1 << level)
     X = sympy.symbols(f"x0:{dim}", real=True)
-    monos = _monomials(X)
+    monos = _monomials(X, order)
     rng = np.random.default_rng(seed)
     xa = np.full(dim, 0.5)
 
@@ -86,17 +94,27 @@ def hand_rows(dim, level=2, seed=11):
     Nsym = sympy.Symbol("N")
     dNs = sympy.symbols(f"dN0:{dim}")
     args = list(X) + [Nsym] + list(dNs)
-    gp = np.array([-1.0, 1.0]) / math.sqrt(3.0)
+    if order == 1:
+        gp, gw = np.array([-1.0, 1.0]) / math.sqrt(3.0), np.array([1.0, 1.0])
+    else:
+        gp, gw = np.array([-math.sqrt(0.6), 0.0, math.sqrt(0.6)]), np.array([5.0, 8.0, 5.0]) / 9.0
+    ng = gp.shape[0]
     wdet = (h / 2.0) ** dim
 
     terms = [dict() for _ in range(dim + 3)]
     radicands = []
     for side in range(1 << dim):
         s = [1 if (side >> k) & 1 else -1 for k in range(dim)]
-        # hat function of x_A on this element
+        # basis function of x_A on this element: Q1 hat, or the quadratic Lagrange factor of
+        # the element end at x_A (local xi = -1 on the element to the right of x_A, +1 on the
+        # one to its left)
         hat = sympy.Integer(1)
         for k in range(dim):
-            hat = hat * (1 - s[k] * (X[k] - float(xa[k])) / h)
+            if order == 1:
+                hat = hat * (1 - s[k] * (X[k] - float(xa[k])) / h)
+            else:
+                xi = 2 * (X[k] - float(xa[k] + s[k] * h / 2)) / h
+                hat = hat * (xi * (xi - 1) / 2 if s[k] > 0 else xi * (xi + 1) / 2)
         F = lambda pb: pb[0] + sympy.Float(pb[1]) * hat
         vo_e = [F(vo[k]) for k in range(dim)]
         vn_e = [vo_e[k] + F(dv[k]) for k in range(dim)]
@@ -172,24 +190,27 @@ def hand_rows(dim, level=2, seed=11):
             "Cn^2 (d_i q, d_i phi)": Cn ** 2 * sum(dNs[i] * D(phit, i) for i in range(dim)),
         })
 
-        # Gauss points of this element, the test function N_A and its gradient there
+        # Gauss points of this element, their weights, the test function N_A and its gradient
         centre = xa + np.array(s) * h / 2.0
-        pts = np.array([centre + np.array([gp[(q >> k) & 1] for k in range(dim)]) * h / 2.0
-                        for q in range(1 << dim)])
-        fac = 1.0 - np.array(s)[None, :] * (pts - xa[None, :]) / h
-        Nv = np.prod(fac, axis=1)
-        dNv = np.stack([-(s[k] / h) * np.prod(np.delete(fac, k, axis=1), axis=1) for k in range(dim)], axis=1)
-        vals_in = [pts[:, k] for k in range(dim)] + [Nv] + [dNv[:, k] for k in range(dim)]
+        qidx = [[(q // ng ** k) % ng for k in range(dim)] for q in range(ng ** dim)]
+        pts = np.array([centre + np.array([gp[i[k]] for k in range(dim)]) * h / 2.0 for i in qidx])
+        wts = np.array([np.prod([gw[i[k]] for k in range(dim)]) for i in qidx])
+        fN = sympy.lambdify(X, hat, "numpy")
+        fdN = [sympy.lambdify(X, sympy.diff(hat, X[k]), "numpy") for k in range(dim)]
+        cols = [pts[:, k] for k in range(dim)]
+        Nv = np.broadcast_to(fN(*cols), (pts.shape[0],)).astype(float)
+        dNv = np.stack([np.broadcast_to(f(*cols), (pts.shape[0],)) for f in fdN], axis=1).astype(float)
+        vals_in = cols + [Nv] + [dNv[:, k] for k in range(dim)]
         for r, row in enumerate(rows):
             for name, expr in row.items():
-                vals = sympy.lambdify(args, expr, "numpy")(*vals_in)
-                terms[r][name] = terms[r].get(name, 0.0) + float(np.sum(np.broadcast_to(vals, Nv.shape))) * wdet
+                vals = sympy.lambdify(args, expr, "numpy", cse=True)(*vals_in)
+                terms[r][name] = terms[r].get(name, 0.0) + float(np.sum(np.broadcast_to(vals, Nv.shape) * wts)) * wdet
         radicands.append(np.asarray(sympy.lambdify(X, rad_m, "numpy")(*[pts[:, k] for k in range(dim)])))
 
     # radicands stay positive at every Gauss point
     assert all(np.all(r > 0) for r in radicands)
     # nodal values of the same fields on the uniform mesh (the hat is 1 at x_A, 0 elsewhere)
-    m = Mesh(dim, level, synth.uniform_leaves(dim, level))
+    m = Mesh(dim, level, synth.uniform_leaves(dim, level)) if order == 1 else MeshQ2(dim, level)
     node = int(np.argmin(np.abs(m.x - xa).sum(axis=1)))
     assert np.abs(m.x[node] - xa).max() < 1e-15 and not m.boundary[node]
 
@@ -204,11 +225,11 @@ def hand_rows(dim, level=2, seed=11):
     return m, Params(**prm), node, U_old, U_new, terms
 
 
-def compare(oracle_cls, dim):
+def compare(oracle_cls, dim, order=1):
     """Largest |oracle row - sum of hand terms| relative to the sum of |terms|, over the
     d + 3 rows of the node, and the smallest |term| relative to the same scale."""
     import torch
-    m, prm, node, U_old, U_new, terms = hand_rows(dim)
+    m, prm, node, U_old, U_new, terms = hand_rows(dim, order=order)
     o = oracle_cls(m)
     R = o.residual(prm, torch.tensor(U_old), torch.tensor(U_new)).numpy()
     err, small = 0.0, 1.0
@@ -229,3 +250,12 @@ def test_every_definition2_term_at_an_interior_node(dim):
     assert err < 1e-12, err
     # every term is visible: a sign flip of any of them moves its row by 2|term|
     assert small > 1e-6, small
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_every_definition2_term_at_an_interior_node_q2(dim):
+    """The same term-by-term evaluation on Q2 elements: the pure second derivatives of the
+    strong residuals (eta lap v, d_i phi lap phi + d_i phi d_ii phi, lap mu) are non-zero."""
+    err, small = compare(Oracle, dim, order=2)
+    assert err < 1e-12, err
+    assert small > 1e-7, small
