@@ -246,7 +246,10 @@ chns_status chns_initial_mu(const chns_mesh* mesh, const chns_params* params, do
  * and the transposed nodal block-Jacobi (J = dR/dU^{k+1} at (U_old, U_new); P is the
  * pressure-level normalisation of pin mode 2), then write the cotangents
  * gU_old = -(dR/dU^k)^T lambda (+ the normalisation's share on p^k) and
- * *gCn = -(dR/dCn)^T lambda.  opts: restart, max_krylov, krylov_rtol are used.
+ * *gCn = -(dR/dCn)^T lambda.  opts: restart, max_krylov, krylov_rtol and pc_type / pc_degree
+ * are used (pc_type >= 1 adds the pressure Schur approximation of the Newton step to the
+ * transposed block-Jacobi -- it is symmetric -- as a Chebyshev polynomial (1, 2) or a
+ * multigrid V-cycle (3, 4); the Cahn-Hilliard block of 2 / 4 is not used here).
  * U_old, U_new, g, lambda, gU_old: device N * n_f doubles; gCn: device double or NULL.
  * Synchronises the stream; CHNS_ENOCONV if GMRES stops short of krylov_rtol. */
 chns_status chns_step_adjoint(const chns_mesh* mesh, const chns_params* params, const chns_solver_opts* opts,

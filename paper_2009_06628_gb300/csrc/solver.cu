@@ -1162,63 +1162,47 @@ int mg_vcycle(MGHier* mg, int l, const float* ce0, cudaStream_t st) {
     return nk;
 }
 
-}  // namespace
-
-extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* p, const chns_solver_opts* o,
-                                        const double* U_old, double* U, chns_stats* stats, void* stream) {
-    if (chns_require_q1(mc, "chns_newton_step") != CHNS_OK) return CHNS_EINVAL;
-    chns_mesh* m = const_cast<chns_mesh*>(mc);
-    PhysConst pc;
-    chns_status st = chns_check_params(mc, p, &pc);
-    if (st != CHNS_OK) return st;
-    if (!o || !U_old || !U) { chns_set_error("null argument"); return CHNS_EINVAL; }
-    if ((st = chns_check_rows(mc, U_old, 8)) != CHNS_OK || (st = chns_check_rows(mc, U, 8)) != CHNS_OK) return st;
-    if (o->restart < 1 || o->restart > MAXSC / 4 || o->max_krylov < 1 || o->max_newton < 0 ||
-        (o->precision != 0 && o->precision != 1) || (o->pc_type < 0 || o->pc_type > 4) ||
-        (o->pc_type >= 1 && (o->pc_degree < 2 || o->pc_degree > 200))) {
-        chns_set_error("bad solver options (restart in [1, 256], max_krylov >= 1, precision 0/1, pc_type 0..4, "
-                       "pc_degree in [2, 200])");
-        return CHNS_EINVAL;
-    }
-    if ((st = ensure_ws(m, o->restart)) != CHNS_OK) return st;
-    SolverWS* ws = m->ws;
-    Ctx c{m, ws, (cudaStream_t)stream, ws->n, 0};
-    c.g = grid_for(c.n);
-    const int D = m->dm.dim, NF = m->dm.nf, mres = o->restart;
-    const bool mixed = o->precision == 1;
-    const int schur = o->pc_type >= 1 ? 1 : 0;
-    const int chblk = (o->pc_type == 2 || o->pc_type == 4) ? 1 : 0;
-    const bool use_mg = o->pc_type >= 3;   // pressure Schur by a multigrid V-cycle
-    const int pcmask = schur | (chblk << 1);
-    const int gE = (int)((m->dm.E + 255) / 256);
-    const int gN1 = (int)((m->dm.N + 255) / 256);
-    // pressure Schur approximation: diagonal, spectrum bound and Chebyshev coefficients
-    auto schur_setup = [&]() -> chns_status {
+// Pressure Schur-complement preconditioner (pc_type >= 1), shared by the Newton step and
+// the adjoint solve: set-up after the block-Jacobi build has written the element
+// coefficients ws->ce, then applies z_p = (approximation of S^{-1}) v_p, either a
+// Jacobi-Chebyshev polynomial of degree `degree` or one multigrid V-cycle (use_mg).
+struct SchurPC {
+    chns_mesh* m;
+    SolverWS* ws;
+    cudaStream_t s;
+    int degree;
+    bool use_mg;
+    int D, NF, gE, gN1, g;
+    SchurPC(chns_mesh* mm, SolverWS* w, cudaStream_t st, int deg, bool mg)
+        : m(mm), ws(w), s(st), degree(deg), use_mg(mg), D(mm->dm.dim), NF(mm->dm.nf),
+          gE((int)((mm->dm.E + 255) / 256)), gN1((int)((mm->dm.N + 255) / 256)), g(grid_for(w->n)) {}
+    chns_status setup() { return use_mg ? mg_setup() : cheb_setup(); }
+    chns_status cheb_setup() {
         if (ws->kref_dim != D) {
             float K[64], Mr[64];
             kref_host(D, K);
             mref_host(D, Mr);
             CHNS_CUDA(cudaMemcpyToSymbolAsync(c_Kref, K, sizeof(float) * (1 << D) * (1 << D), 0,
-                                              cudaMemcpyHostToDevice, c.s));
+                                              cudaMemcpyHostToDevice, s));
             CHNS_CUDA(cudaMemcpyToSymbolAsync(c_Mref, Mr, sizeof(float) * (1 << D) * (1 << D), 0,
-                                              cudaMemcpyHostToDevice, c.s));
+                                              cudaMemcpyHostToDevice, s));
             ws->kref_dim = D;
         }
         const int64_t N = m->dm.N;
-        CHNS_CUDA(cudaMemsetAsync(ws->kdinv, 0, N * sizeof(float), c.s));
-        CHNS_CUDA(cudaMemsetAsync(ws->kbnd, 0, N * sizeof(float), c.s));
-        CHNS_CUDA(cudaMemsetAsync(ws->kmax, 0, sizeof(unsigned int), c.s));
-        if (D == 2) { schur_diag_kernel<2><<<gE, 256, 0, c.s>>>(m->dm, ws->ce, ws->kdinv, ws->kbnd); chns_count_launches(1); }
-        else { schur_diag_kernel<3><<<gE, 256, 0, c.s>>>(m->dm, ws->ce, ws->kdinv, ws->kbnd); chns_count_launches(1); }
-        { recip_kernel<<<gN1, 256, 0, c.s>>>(ws->kdinv, N); chns_count_launches(1); }
+        CHNS_CUDA(cudaMemsetAsync(ws->kdinv, 0, N * sizeof(float), s));
+        CHNS_CUDA(cudaMemsetAsync(ws->kbnd, 0, N * sizeof(float), s));
+        CHNS_CUDA(cudaMemsetAsync(ws->kmax, 0, sizeof(unsigned int), s));
+        if (D == 2) { schur_diag_kernel<2><<<gE, 256, 0, s>>>(m->dm, ws->ce, ws->kdinv, ws->kbnd); chns_count_launches(1); }
+        else { schur_diag_kernel<3><<<gE, 256, 0, s>>>(m->dm, ws->ce, ws->kdinv, ws->kbnd); chns_count_launches(1); }
+        { recip_kernel<<<gN1, 256, 0, s>>>(ws->kdinv, N); chns_count_launches(1); }
         // The Chebyshev interval must not cut the top of the spectrum of D^{-1} K, where
         // the polynomial would amplify.  Gershgorin with the row-sum bounds gives it for
         // any positive D: 2 on a uniform mesh (off-diagonal stiffness entries are <= 0),
         // more where hanging constraints fold positive weights into a row.
-        { gershgorin_max_kernel<<<c.g, 256, 0, c.s>>>(ws->kbnd, ws->kdinv, N, ws->kmax); chns_count_launches(1); }
+        { gershgorin_max_kernel<<<g, 256, 0, s>>>(ws->kbnd, ws->kdinv, N, ws->kmax); chns_count_launches(1); }
         unsigned int kbits = 0;
-        CHNS_CUDA(cudaMemcpyAsync(&ws->hsc[0], ws->kmax, sizeof(unsigned int), cudaMemcpyDeviceToHost, c.s));
-        CHNS_CUDA(cudaStreamSynchronize(c.s));
+        CHNS_CUDA(cudaMemcpyAsync(&ws->hsc[0], ws->kmax, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+        CHNS_CUDA(cudaStreamSynchronize(s));
         std::memcpy(&kbits, &ws->hsc[0], sizeof(unsigned int));
         float kb;
         std::memcpy(&kb, &kbits, sizeof(float));
@@ -1228,7 +1212,7 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
         const double ratio = std::max(16.0, nside * nside / 8.0);
         const double alpha = beta / ratio;
         const double theta = 0.5 * (beta + alpha), delta = 0.5 * (beta - alpha), sigma = theta / delta;
-        const int deg = o->pc_degree;
+        const int deg = degree;
         ws->cheb_c1.assign(deg, 0.0f);
         ws->cheb_c2.assign(deg, 0.0f);
         double rho = 1.0 / sigma;
@@ -1241,18 +1225,16 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
         ws->cheb_inv_theta = (float)(1.0 / theta);
         ws->schur_gen++;   // captured applies hold the old coefficients
         return CHNS_OK;
-    };
-    // geometric multigrid set-up: coarse coefficients, diagonals, Gershgorin bounds and the
-    // Chebyshev smoothers of every level (one read-back for all bounds)
-    auto mg_setup = [&]() -> chns_status {
+    }
+    chns_status mg_setup() {
         if (ws->kref_dim != D) {
             float K[64], Mr[64];
             kref_host(D, K);
             mref_host(D, Mr);
             CHNS_CUDA(cudaMemcpyToSymbolAsync(c_Kref, K, sizeof(float) * (1 << D) * (1 << D), 0,
-                                              cudaMemcpyHostToDevice, c.s));
+                                              cudaMemcpyHostToDevice, s));
             CHNS_CUDA(cudaMemcpyToSymbolAsync(c_Mref, Mr, sizeof(float) * (1 << D) * (1 << D), 0,
-                                              cudaMemcpyHostToDevice, c.s));
+                                              cudaMemcpyHostToDevice, s));
             ws->kref_dim = D;
         }
         chns_status sb = mg_hier_build(m);
@@ -1262,24 +1244,24 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
         for (int l = 1; l < nl; ++l) {
             MGLevel& C = mg->lv[(size_t)l];
             MGLevel& F = mg->lv[(size_t)l - 1];
-            CHNS_CUDA(cudaMemsetAsync(C.ce, 0, C.E * sizeof(float), c.s));
-            { mg_restrict_ce_kernel<<<(int)((F.E + 255) / 256), 256, 0, c.s>>>(F.E, D, C.fmap, F.dm.level, C.dm.level, l == 1 ? ws->ce : F.ce, C.ce); chns_count_launches(1); }
+            CHNS_CUDA(cudaMemsetAsync(C.ce, 0, C.E * sizeof(float), s));
+            { mg_restrict_ce_kernel<<<(int)((F.E + 255) / 256), 256, 0, s>>>(F.E, D, C.fmap, F.dm.level, C.dm.level, l == 1 ? ws->ce : F.ce, C.ce); chns_count_launches(1); }
         }
-        CHNS_CUDA(cudaMemsetAsync(mg->kmax, 0, nl * sizeof(unsigned int), c.s));
+        CHNS_CUDA(cudaMemsetAsync(mg->kmax, 0, nl * sizeof(unsigned int), s));
         for (int l = 0; l < nl; ++l) {
             MGLevel& L = mg->lv[(size_t)l];
             const float* cel = l == 0 ? ws->ce : L.ce;
             const int gEl = (int)((L.E + 255) / 256), gNl = (int)((L.N + 255) / 256);
-            CHNS_CUDA(cudaMemsetAsync(L.dinv, 0, L.N * sizeof(float), c.s));
-            CHNS_CUDA(cudaMemsetAsync(L.bnd, 0, L.N * sizeof(float), c.s));
-            if (D == 2) { schur_diag_kernel<2><<<gEl, 256, 0, c.s>>>(L.dm, cel, L.dinv, L.bnd); chns_count_launches(1); }
-            else { schur_diag_kernel<3><<<gEl, 256, 0, c.s>>>(L.dm, cel, L.dinv, L.bnd); chns_count_launches(1); }
-            { recip_kernel<<<gNl, 256, 0, c.s>>>(L.dinv, L.N); chns_count_launches(1); }
-            { gershgorin_max_kernel<<<grid_for(L.N), 256, 0, c.s>>>(L.bnd, L.dinv, L.N, mg->kmax + l); chns_count_launches(1); }
+            CHNS_CUDA(cudaMemsetAsync(L.dinv, 0, L.N * sizeof(float), s));
+            CHNS_CUDA(cudaMemsetAsync(L.bnd, 0, L.N * sizeof(float), s));
+            if (D == 2) { schur_diag_kernel<2><<<gEl, 256, 0, s>>>(L.dm, cel, L.dinv, L.bnd); chns_count_launches(1); }
+            else { schur_diag_kernel<3><<<gEl, 256, 0, s>>>(L.dm, cel, L.dinv, L.bnd); chns_count_launches(1); }
+            { recip_kernel<<<gNl, 256, 0, s>>>(L.dinv, L.N); chns_count_launches(1); }
+            { gershgorin_max_kernel<<<grid_for(L.N), 256, 0, s>>>(L.bnd, L.dinv, L.N, mg->kmax + l); chns_count_launches(1); }
         }
         CHNS_CUDA(cudaGetLastError());
-        CHNS_CUDA(cudaMemcpyAsync(ws->hsc, mg->kmax, nl * sizeof(unsigned int), cudaMemcpyDeviceToHost, c.s));
-        CHNS_CUDA(cudaStreamSynchronize(c.s));
+        CHNS_CUDA(cudaMemcpyAsync(ws->hsc, mg->kmax, nl * sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+        CHNS_CUDA(cudaStreamSynchronize(s));
         for (int l = 0; l < nl; ++l) {
             MGLevel& L = mg->lv[(size_t)l];
             unsigned int kbits = 0;
@@ -1291,7 +1273,7 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
             const double beta = 1.01 * (double)kb;
             if (l + 1 < nl) {
                 // smoother: damp the upper part of the spectrum of D^{-1} K
-                L.deg = o->pc_degree;
+                L.deg = degree;
                 cheb_coeffs(beta / 10.0, beta, L.deg, L.c1, L.c2, L.inv_theta);
             } else {
                 // coarsest level: one long sweep over the whole spectrum
@@ -1302,11 +1284,9 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
         }
         ws->schur_gen++;   // captured applies hold the old coefficients
         return CHNS_OK;
-    };
-    // z_p = (Chebyshev approximation of S^{-1}) v_p, strided input and output
-    auto schur_apply_any = [&](auto vin, auto zout) -> chns_status {
-        using TI = std::remove_const_t<std::remove_pointer_t<decltype(vin)>>;
-        using TO = std::remove_pointer_t<decltype(zout)>;
+    }
+    template <class TI, class TO>
+    chns_status apply(const TI* vin, TO* zout) {
         const int64_t N = m->dm.N;
         // the apply is a sequence of short launches: replayed from a CUDA graph
         auto enqueue = [&](cudaStream_t st) -> int {
@@ -1318,13 +1298,13 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                 return nv + 2;
             }
             cheb_init_kernel<TI><<<gN1, 256, 0, st>>>(N, NF, D, vin, ws->kdinv, ws->cr, ws->cx, ws->cd, ws->cy, ws->cheb_inv_theta);
-            for (int k = 0; k + 1 < o->pc_degree; ++k) {
+            for (int k = 0; k + 1 < degree; ++k) {
                 if (D == 2) schur_matvec_kernel<2><<<gE, 256, 0, st>>>(m->dm, ws->ce, ws->cd, ws->cy);
                 else schur_matvec_kernel<3><<<gE, 256, 0, st>>>(m->dm, ws->ce, ws->cd, ws->cy);
                 cheb_step_kernel<<<gN1, 256, 0, st>>>(N, ws->kdinv, ws->cr, ws->cx, ws->cd, ws->cy, ws->cheb_c1[k], ws->cheb_c2[k]);
             }
             cheb_final_kernel<TO><<<gN1, 256, 0, st>>>(N, NF, D, ws->cx, ws->cd, zout);
-            return 2 + 2 * (o->pc_degree - 1);
+            return 2 + 2 * (degree - 1);
         };
         if (!ws->no_graphs) {
             SolverWS::SchurGraph* hit = nullptr;
@@ -1362,15 +1342,49 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                 }
             }
             if (hit) {
-                CHNS_CUDA(cudaGraphLaunch(hit->exec, c.s));
+                CHNS_CUDA(cudaGraphLaunch(hit->exec, s));
                 chns_count_launches(hit->nk);
                 return CHNS_OK;
             }
         }
-        chns_count_launches(enqueue(c.s));
+        chns_count_launches(enqueue(s));
         CHNS_CUDA(cudaGetLastError());
         return CHNS_OK;
-    };
+    }
+};
+
+}  // namespace
+
+extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* p, const chns_solver_opts* o,
+                                        const double* U_old, double* U, chns_stats* stats, void* stream) {
+    if (chns_require_q1(mc, "chns_newton_step") != CHNS_OK) return CHNS_EINVAL;
+    chns_mesh* m = const_cast<chns_mesh*>(mc);
+    PhysConst pc;
+    chns_status st = chns_check_params(mc, p, &pc);
+    if (st != CHNS_OK) return st;
+    if (!o || !U_old || !U) { chns_set_error("null argument"); return CHNS_EINVAL; }
+    if ((st = chns_check_rows(mc, U_old, 8)) != CHNS_OK || (st = chns_check_rows(mc, U, 8)) != CHNS_OK) return st;
+    if (o->restart < 1 || o->restart > MAXSC / 4 || o->max_krylov < 1 || o->max_newton < 0 ||
+        (o->precision != 0 && o->precision != 1) || (o->pc_type < 0 || o->pc_type > 4) ||
+        (o->pc_type >= 1 && (o->pc_degree < 2 || o->pc_degree > 200))) {
+        chns_set_error("bad solver options (restart in [1, 256], max_krylov >= 1, precision 0/1, pc_type 0..4, "
+                       "pc_degree in [2, 200])");
+        return CHNS_EINVAL;
+    }
+    if ((st = ensure_ws(m, o->restart)) != CHNS_OK) return st;
+    SolverWS* ws = m->ws;
+    Ctx c{m, ws, (cudaStream_t)stream, ws->n, 0};
+    c.g = grid_for(c.n);
+    const int D = m->dm.dim, NF = m->dm.nf, mres = o->restart;
+    const bool mixed = o->precision == 1;
+    const int schur = o->pc_type >= 1 ? 1 : 0;
+    const int chblk = (o->pc_type == 2 || o->pc_type == 4) ? 1 : 0;
+    const bool use_mg = o->pc_type >= 3;   // pressure Schur by a multigrid V-cycle
+    const int pcmask = schur | (chblk << 1);
+    const int gE = (int)((m->dm.E + 255) / 256);
+    const int gN1 = (int)((m->dm.N + 255) / 256);
+    SchurPC spc(m, ws, c.s, o->pc_degree, use_mg);
+    auto schur_apply_any = [&](auto vin, auto zout) -> chns_status { return spc.apply(vin, zout); };
     const int pin = p->pin_pressure;
     const int gN = (int)((m->dm.N + 127) / 128);
     chns_stats S;
@@ -1489,7 +1503,7 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
         }
         CHNS_CUDA(cudaGetLastError());
         if (schur) {
-            chns_status st3 = use_mg ? mg_setup() : schur_setup();
+            chns_status st3 = spc.setup();
             if (st3 != CHNS_OK) return st3;
         }
         if (chblk) {
@@ -1878,8 +1892,9 @@ extern "C" chns_status chns_step_adjoint(const chns_mesh* mc, const chns_params*
     if (st != CHNS_OK) return st;
     if (!o || !U_old || !U_new || !g || !lambda || !gU_old) { chns_set_error("null argument"); return CHNS_EINVAL; }
     if ((st = chns_check_rows(mc, U_old, 8)) != CHNS_OK || (st = chns_check_rows(mc, U_new, 8)) != CHNS_OK) return st;
-    if (o->restart < 1 || o->restart > MAXSC / 4 || o->max_krylov < 1) {
-        chns_set_error("bad solver options (restart in [1, 256], max_krylov >= 1)");
+    if (o->restart < 1 || o->restart > MAXSC / 4 || o->max_krylov < 1 || o->pc_type < 0 || o->pc_type > 4 ||
+        (o->pc_type >= 1 && (o->pc_degree < 2 || o->pc_degree > 200))) {
+        chns_set_error("bad solver options (restart in [1, 256], max_krylov >= 1, pc_type 0..4, pc_degree in [2, 200])");
         return CHNS_EINVAL;
     }
     if ((st = ensure_ws(m, o->restart)) != CHNS_OK) return st;
@@ -1887,6 +1902,10 @@ extern "C" chns_status chns_step_adjoint(const chns_mesh* mc, const chns_params*
     Ctx c{m, ws, (cudaStream_t)stream, ws->n, 0};
     c.g = grid_for(c.n);
     const int D = m->dm.dim, NF = m->dm.nf, mres = o->restart, pin = p->pin_pressure;
+    // the pressure Schur approximation is symmetric, so J^T takes it as J does; the
+    // Cahn-Hilliard block of pc_type 2 / 4 is not used here
+    const bool schur = o->pc_type >= 1;
+    SchurPC spc(m, ws, c.s, o->pc_degree, o->pc_type >= 3);
     const int gN = (int)((m->dm.N + 127) / 128);
     const int nbk = c.g < 1024 ? c.g : 1024;
     chns_stats S;
@@ -1896,7 +1915,8 @@ extern "C" chns_status chns_step_adjoint(const chns_mesh* mc, const chns_params*
     cudaError_t ce = (D == 2) ? pc_build_launch<2, double>(m, pc, U_old, U_new, ws->Pblk64, ws->ce, c.s)
                               : pc_build_launch<3, double>(m, pc, U_old, U_new, ws->Pblk64, ws->ce, c.s);
     CHNS_CUDA(ce);
-    { pc_invert_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm, ws->Pblk64, ws->Pinv64, pin, ws->S, ws->Sd, 0); chns_count_launches(1); }
+    { pc_invert_kernel<double, double><<<gN, 128, 0, c.s>>>(m->dm, ws->Pblk64, ws->Pinv64, pin, ws->S, ws->Sd, schur ? 1 : 0); chns_count_launches(1); }
+    if (schur && (st = spc.setup()) != CHNS_OK) return st;
     // pin mode 2: J' = J + u m_p^T / |Omega| with u = |diag J| on the pressure rows is
     // nonsingular, and J'^T lambda = P^T g has the solution of J^T lambda = P^T g with
     // u^T lambda = 0 (GMRES on the singular J^T drifts along its null vector)
@@ -1937,6 +1957,7 @@ extern "C" chns_status chns_step_adjoint(const chns_mesh* mc, const chns_params*
             for (; j < mres && kry < o->max_krylov; ++j, ++kry) {
                 double* Vj = ws->V + (size_t)j * c.n;
                 { pc_apply_T_kernel<double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv64, Vj, ws->z64); chns_count_launches(1); }
+                if (schur && (st = spc.apply((const double*)Vj, ws->z64)) != CHNS_OK) return st;
                 CHNS_CUDA(launch_vjp(m, pc, U_old, U_new, ws->z64, ws->w, nullptr, nullptr, pin, c.s));
                 if (pin == 2) add_pmean_T(ws->z64, ws->w);
                 S.jvp_calls++;
@@ -1987,6 +2008,7 @@ extern "C" chns_status chns_step_adjoint(const chns_mesh* mc, const chns_params*
             CHNS_CUDA(cudaMemcpyAsync(ws->sc, ws->hsc, k * sizeof(double), cudaMemcpyHostToDevice, c.s));
             { combine_kernel<<<c.g, 256, 0, c.s>>>(ws->V, c.n, k, ws->sc, ws->t64, c.n); chns_count_launches(1); }
             { pc_apply_T_kernel<double><<<gN, 128, 0, c.s>>>(m->dm.N, NF, ws->Pinv64, ws->t64, ws->z64); chns_count_launches(1); }
+            if (schur && (st = spc.apply((const double*)ws->t64, ws->z64)) != CHNS_OK) return st;
             { axpy_kernel<<<c.g, 256, 0, c.s>>>(1.0, ws->z64, lambda, c.n); chns_count_launches(1); }
             CHNS_CUDA(cudaGetLastError());
             if (done || kry >= o->max_krylov) break;
