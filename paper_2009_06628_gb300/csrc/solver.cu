@@ -65,6 +65,9 @@ struct SolverWS {
     cudaStream_t cap = nullptr;
     int schur_gen = 0;
     bool no_graphs = false;
+    // CUDA graphs of the Gram-Schmidt sequence of Arnoldi step j (its kernels take k = j + 1
+    // and fixed workspace pointers), captured at first use
+    cudaGraphExec_t orth_exec[257] = {};
     float* kbnd = nullptr;   // N bounds of the absolute row sums of the Schur Laplacian
     unsigned int* kmax = nullptr;  // max_p kbnd[p] / diag[p] (float bits)
     float* cr = nullptr;     // N Chebyshev work vectors
@@ -91,6 +94,8 @@ void chns_solver_ws_free(SolverWS* ws) {
     if (!ws) return;
     for (auto& g : ws->sgraph)
         if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (auto& g : ws->orth_exec)
+        if (g) cudaGraphExecDestroy(g);
     if (ws->cap) cudaStreamDestroy(ws->cap);
     cudaFree(ws->V);
     cudaFree(ws->w);
@@ -1476,16 +1481,23 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
     // one classical Gram-Schmidt pass against V_0..V_{k-1}: h -> hdev[0..k), |w|^2 before
     // -> nrm_before, |w|^2 after -> nrm_after (all device scalars); with pred, every kernel
     // of the pass returns at once when pred[0] == 0
-    auto orth_pass = [&](int k, double* hdev, double* nrm_before, double* nrm_after,
-                         const double* pred) -> chns_status {
+    auto orth_pass = [&](cudaStream_t st, int k, double* hdev, double* nrm_before, double* nrm_after,
+                         const double* pred) {
         int nbx = c.g < ORTH_MAX_BX ? c.g : ORTH_MAX_BX;
         const int nch = (k + 7) / 8;
-        { orth_dots_kernel<<<dim3(nbx, nch), 256, 0, c.s>>>(ws->V, c.n, k, ws->w, c.n, ws->part, pred); chns_count_launches(1); }
-        { orth_dots_final_kernel<<<nch, 288, 0, c.s>>>(ws->part, nbx, k, hdev, nrm_before, pred); chns_count_launches(1); }
-        { gs_update_norm_kernel<<<nbx, 256, 0, c.s>>>(ws->V, c.n, k, hdev, ws->w, c.n, m->d_partials, pred); chns_count_launches(1); }
-        { final_reduce1_pred_kernel<<<1, 256, 0, c.s>>>(m->d_partials, nbx, nrm_after, pred); chns_count_launches(1); }
-        CHNS_CUDA(cudaGetLastError());
-        return CHNS_OK;
+        orth_dots_kernel<<<dim3(nbx, nch), 256, 0, st>>>(ws->V, c.n, k, ws->w, c.n, ws->part, pred);
+        orth_dots_final_kernel<<<nch, 288, 0, st>>>(ws->part, nbx, k, hdev, nrm_before, pred);
+        gs_update_norm_kernel<<<nbx, 256, 0, st>>>(ws->V, c.n, k, hdev, ws->w, c.n, m->d_partials, pred);
+        final_reduce1_pred_kernel<<<1, 256, 0, st>>>(m->d_partials, nbx, nrm_after, pred);
+    };
+    // Gram-Schmidt of Arnoldi step j with device-decided re-orthogonalisation, the next
+    // Arnoldi vector and the read-back of the Hessenberg column: 10 kernels and a copy
+    auto orth_enqueue = [&](cudaStream_t st, int j) {
+        orth_pass(st, j + 1, ws->sc, ws->sc + 600, ws->sc + 601, nullptr);
+        reorth_decide_kernel<<<1, 256, 0, st>>>(ws->sc, j + 1);
+        orth_pass(st, j + 1, ws->sc + 256, ws->sc + 602, ws->sc + 603, ws->sc + 605);
+        scale_next_kernel<<<c.g, 256, 0, st>>>(ws->w, ws->V + (size_t)(j + 1) * c.n, c.n, ws->sc + 603);
+        cudaMemcpyAsync(ws->hsc, ws->sc, 606 * sizeof(double), cudaMemcpyDeviceToHost, st);
     };
     auto build_pc = [&]() -> chns_status {
         CHNS_CUDA(cudaEventRecord(ws->ev[2], c.s));
@@ -1622,14 +1634,34 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
                 // classical Gram-Schmidt with selective re-orthogonalisation (decided on the
                 // device) and the next Arnoldi vector, all queued without a host round trip
                 CHNS_CUDA(cudaEventRecord(ws->ev[6], c.s));
-                chns_status so = orth_pass(j + 1, ws->sc, ws->sc + 600, ws->sc + 601, nullptr);
-                if (so != CHNS_OK) return so;
-                { reorth_decide_kernel<<<1, 256, 0, c.s>>>(ws->sc, j + 1); chns_count_launches(1); }
-                so = orth_pass(j + 1, ws->sc + 256, ws->sc + 602, ws->sc + 603, ws->sc + 605);
-                if (so != CHNS_OK) return so;
-                { scale_next_kernel<<<c.g, 256, 0, c.s>>>(ws->w, ws->V + (size_t)(j + 1) * c.n, c.n, ws->sc + 603); chns_count_launches(1); }
+                {
+                    // replayed from a CUDA graph of this j once captured (the launches are short)
+                    bool done_g = false;
+                    if (!ws->no_graphs && j < 257) {
+                        if (!ws->orth_exec[j]) {
+                            cudaGraph_t gr = nullptr;
+                            cudaGraphExec_t ex = nullptr;
+                            bool ok = ws->cap || cudaStreamCreateWithFlags(&ws->cap, cudaStreamNonBlocking) == cudaSuccess;
+                            if (ok) ok = cudaStreamBeginCapture(ws->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+                            if (ok) {
+                                orth_enqueue(ws->cap, j);
+                                ok = cudaStreamEndCapture(ws->cap, &gr) == cudaSuccess && gr != nullptr;
+                                if (ok) ok = cudaGraphInstantiate(&ex, gr, 0) == cudaSuccess;
+                                if (gr) cudaGraphDestroy(gr);
+                            }
+                            if (ok) ws->orth_exec[j] = ex;
+                            else { (void)cudaGetLastError(); ws->no_graphs = true; }
+                        }
+                        if (ws->orth_exec[j]) {
+                            CHNS_CUDA(cudaGraphLaunch(ws->orth_exec[j], c.s));
+                            done_g = true;
+                        }
+                    }
+                    if (!done_g) orth_enqueue(c.s, j);
+                    chns_count_launches(10);
+                    CHNS_CUDA(cudaGetLastError());
+                }
                 CHNS_CUDA(cudaEventRecord(ws->ev[7], c.s));
-                CHNS_CUDA(cudaMemcpyAsync(ws->hsc, ws->sc, 606 * sizeof(double), cudaMemcpyDeviceToHost, c.s));
                 CHNS_CUDA(cudaEventRecord(ws->ev[10], c.s));
                 // queue the next vector's operator application before reading the scalars, so
                 // the GPU works on it while the host updates the Hessenberg column; if this
