@@ -44,12 +44,12 @@ METRIC = "CHNS JÂ·x GDOF/s & % HBM roofline; mixed vs FP64 Newton step time at â
 # preconditioner of the timed Newton step (chns_solver_opts.pc_type)
 BENCH_PC_TYPE = 1
 KERNEL_SRC_FILES = ("paper_2009_06628_gb300/csrc/element_kernels.cu", "paper_2009_06628_gb300/csrc/pointwise.cuh")
-KERNEL_SRC_SHA = "b00d8611c066543e"
+KERNEL_SRC_SHA = "de8fd3eb9c4ab80e"
 KERNEL_COUNTS = {
-    "jvp_fp32": {"flop_per_element": 14769.6, "dram_bytes": 35049472},
-    "jvp_fp64": {"flop_per_element": 15161.6, "dram_bytes": 61910784},
-    "residual_fp64": {"flop_per_element": 9688.0, "dram_bytes": 48280576},
-    "vjp_fp64": {"flop_per_element": 20768.0, "dram_bytes": 77111296},
+    "jvp_fp32": {"flop_per_element": 14769.6, "dram_bytes": 35048192},
+    "jvp_fp64": {"flop_per_element": 15168.0, "dram_bytes": 61910016},
+    "residual_fp64": {"flop_per_element": 9688.0, "dram_bytes": 48285440},
+    "vjp_fp64": {"flop_per_element": 20776.0, "dram_bytes": 77077760},
 }
 
 
