@@ -363,7 +363,8 @@ def run_trajectory(args):
     chns.initial_mu(gm, prm, U0)
     dof = U0.numel()
     kw = dict(rtol=1e-9, atol=1e-14, krylov_rtol=1e-3, restart=args.restart, max_krylov=args.max_krylov,
-              pc_type=args.pc_type, pc_degree=args.pc_degree or (3 if args.pc_type >= 3 else 16))
+              pc_type=args.pc_type, pc_degree=args.pc_degree or (3 if args.pc_type >= 3 else 16),
+              ew_eta0=args.ew_eta0)
     o32 = chns.SolverOpts.make(precision=1, **kw)
     o64 = chns.SolverOpts.make(precision=0, **kw)
     fields = {"v": slice(0, d), "p": slice(d, d + 1), "phi": slice(d + 1, d + 2), "mu": slice(d + 2, d + 3)}
@@ -430,6 +431,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--max-krylov", type=int, default=5000)
+    ap.add_argument("--ew-eta0", type=float, default=0.0,
+                    help="--run: Eisenstat-Walker forcing from this first tolerance (0: fixed krylov_rtol)")
     ap.add_argument("--pc-type", type=int, default=None,
                     help="preconditioner (default: 1 for the bench step and --run)")
     ap.add_argument("--pc-degree", type=int, default=None,

@@ -92,7 +92,11 @@ typedef struct {
  * right preconditioning) to relative tolerance eta = max(krylov_rtol, min(0.5,
  * 0.1 * target / ||S R||)) with target = max(atol, rtol ||S R(U^0)||) (the last linear
  * solve is not driven further than the Newton target needs), at most max_krylov
- * iterations per Newton iteration. */
+ * iterations per Newton iteration.  With ew_eta0 > 0 the fixed krylov_rtol in that
+ * formula is replaced by the adaptive forcing term of Eisenstat and Walker (SIAM J. Sci.
+ * Comput. 17, 1996, choice 2 with gamma = 0.9, alpha = 2 and their safeguard):
+ * eta_0 = ew_eta0, eta_k = 0.9 (||S R_k|| / ||S R_{k-1}||)^2, raised to 0.9 eta_{k-1}^2
+ * when that exceeds 0.1, and clamped to [krylov_rtol, 0.9]. */
 typedef struct {
     double rtol, atol, krylov_rtol;
     int32_t max_newton, max_krylov, restart, precision;
@@ -113,6 +117,13 @@ typedef struct {
                             (host work and device memory held by the mesh) on the first call
                             that asks for it. */
     int32_t pc_degree;   /* Chebyshev degree for pc_type 1/2 (whole apply) or 3/4 (smoother), in [2, 200] */
+    double ew_eta0;      /* 0: fixed forcing term (krylov_rtol); in (0, 1): Eisenstat-Walker
+                            forcing starting from this tolerance; anything else is CHNS_EINVAL.
+                            The Newton step's first linear solve is then loose: at U^{k+1} = U^k
+                            the residual is led by the pressure rows (the stabilisation term
+                            carries the momentum imbalance before the time derivative has
+                            responded), and the first Newton iteration is limited by the
+                            nonlinearity rather than by the linear solve. */
 } chns_solver_opts;
 
 #define CHNS_HIST 32
@@ -247,7 +258,7 @@ chns_status chns_initial_mu(const chns_mesh* mesh, const chns_params* params, do
  * pressure-level normalisation of pin mode 2), then write the cotangents
  * gU_old = -(dR/dU^k)^T lambda (+ the normalisation's share on p^k) and
  * *gCn = -(dR/dCn)^T lambda.  opts: restart, max_krylov, krylov_rtol and pc_type / pc_degree
- * are used (pc_type >= 1 adds the pressure Schur approximation of the Newton step to the
+ * are used, ew_eta0 is not (one linear solve) (pc_type >= 1 adds the pressure Schur approximation of the Newton step to the
  * transposed block-Jacobi -- it is symmetric -- as a Chebyshev polynomial (1, 2) or a
  * multigrid V-cycle (3, 4); the Cahn-Hilliard block of 2 / 4 is not used here).
  * U_old, U_new, g, lambda, gU_old: device N * n_f doubles; gCn: device double or NULL.

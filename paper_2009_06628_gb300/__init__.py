@@ -44,13 +44,14 @@ class Params(ctypes.Structure):
 class SolverOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("atol", ctypes.c_double), ("krylov_rtol", ctypes.c_double),
                 ("max_newton", ctypes.c_int32), ("max_krylov", ctypes.c_int32), ("restart", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("pc_type", ctypes.c_int32), ("pc_degree", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("pc_type", ctypes.c_int32), ("pc_degree", ctypes.c_int32),
+                ("ew_eta0", ctypes.c_double)]
 
     @classmethod
     def make(cls, rtol=1e-9, atol=1e-14, krylov_rtol=1e-3, max_newton=20, max_krylov=2000, restart=60,
-             precision=1, pc_type=1, pc_degree=8):
+             precision=1, pc_type=1, pc_degree=8, ew_eta0=0.0):
         return cls(rtol=rtol, atol=atol, krylov_rtol=krylov_rtol, max_newton=max_newton, max_krylov=max_krylov,
-                   restart=restart, precision=precision, pc_type=pc_type, pc_degree=pc_degree)
+                   restart=restart, precision=precision, pc_type=pc_type, pc_degree=pc_degree, ew_eta0=ew_eta0)
 
 
 class Stats(ctypes.Structure):

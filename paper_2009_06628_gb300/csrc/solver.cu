@@ -1371,9 +1371,10 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
     if ((st = chns_check_rows(mc, U_old, 8)) != CHNS_OK || (st = chns_check_rows(mc, U, 8)) != CHNS_OK) return st;
     if (o->restart < 1 || o->restart > MAXSC / 4 || o->max_krylov < 1 || o->max_newton < 0 ||
         (o->precision != 0 && o->precision != 1) || (o->pc_type < 0 || o->pc_type > 4) ||
-        (o->pc_type >= 1 && (o->pc_degree < 2 || o->pc_degree > 200))) {
+        (o->pc_type >= 1 && (o->pc_degree < 2 || o->pc_degree > 200)) ||
+        !(o->ew_eta0 == 0.0 || (o->ew_eta0 > 0.0 && o->ew_eta0 < 1.0))) {
         chns_set_error("bad solver options (restart in [1, 256], max_krylov >= 1, precision 0/1, pc_type 0..4, "
-                       "pc_degree in [2, 200])");
+                       "pc_degree in [2, 200], ew_eta0 0 or in (0, 1))");
         return CHNS_EINVAL;
     }
     if ((st = ensure_ws(m, o->restart)) != CHNS_OK) return st;
@@ -1533,6 +1534,7 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
         { final_reduce_kernel<<<1, 256, 0, c.s>>>(m->d_partials, nbm, 1, ws->sc + 610); chns_count_launches(1); }
     };
     bool pc_pending = false;
+    double eta_prev = 0.0, rn_prev = 0.0;   // previous forcing term and residual (Eisenstat-Walker)
     for (int it = 0;; ++it) {
         CHNS_CUDA(launch_residual(m, pc, U_old, U, ws->R, pin, c.s));
         if (it == 0) {
@@ -1577,10 +1579,26 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
             rnorm = std::sqrt(bb);
         }
         const double bnorm_s = rnorm;
-        // forcing term: krylov_rtol, relaxed once the Newton target is near (a solve
-        // below a tenth of what the target needs is wasted)
+        // forcing term: krylov_rtol (or the Eisenstat-Walker term with ew_eta0 > 0),
+        // relaxed once the Newton target is near (a solve below a tenth of what the
+        // target needs is wasted)
         const double target = std::max(o->atol, o->rtol * r0);
-        const double eta = std::max(o->krylov_rtol, std::min(0.5, 0.1 * target / rn));
+        double eta_k = o->krylov_rtol;
+        if (o->ew_eta0 > 0.0) {
+            // Eisenstat-Walker choice 2 (gamma 0.9, alpha 2) with their safeguard
+            if (it == 0) {
+                eta_k = o->ew_eta0;
+            } else {
+                const double ratio = rn / rn_prev;
+                eta_k = 0.9 * ratio * ratio;
+                const double guard = 0.9 * eta_prev * eta_prev;
+                if (guard > 0.1) eta_k = std::max(eta_k, guard);
+            }
+            eta_k = std::min(0.9, std::max(o->krylov_rtol, eta_k));
+        }
+        const double eta = std::max(eta_k, std::min(0.5, 0.1 * target / rn));
+        eta_prev = eta_k;
+        rn_prev = rn;
         // w = S J M^{-1} S^{-1} V_j (similarity scaling: the eigenvalues are those of J M^{-1});
         // the J x / apply timing events come from set es (two sets alternate, so the next
         // vector's application can be queued before this one's events are read)
