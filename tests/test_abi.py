@@ -78,3 +78,35 @@ def test_rejects_bad_arguments(chns):
     with pytest.raises(chns.ChnsError) as e:
         chns.Mesh(2, 2, leaves, lo=1.0, hi=0.0)
     assert e.value.name == "CHNS_EINVAL"
+
+
+def test_struct_layouts_match_the_header(chns, tmp_path):
+    """The ctypes mirrors of chns_params, chns_solver_opts and chns_stats have the size and
+    the field offsets that a C compiler gives the structs of include/chns.h (a field added
+    on one side only, or reordered, fails here before any call passes a misread struct)."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"chns_params": chns.Params, "chns_solver_opts": chns.SolverOpts, "chns_stats": chns.Stats}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "chns.h"', "int main(void) {",
+             '  printf("chns_leaf %zu\\n", sizeof(chns_leaf));']
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                text=True).stdout.splitlines())
+    assert int(out["chns_leaf"]) == 16
+    for cname, py in structs.items():
+        assert int(out[cname]) == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(out[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)
