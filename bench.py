@@ -364,17 +364,30 @@ def run_trajectory(args):
     dof = U0.numel()
     kw = dict(rtol=1e-9, atol=1e-14, krylov_rtol=1e-3, restart=args.restart, max_krylov=args.max_krylov,
               pc_type=args.pc_type, pc_degree=args.pc_degree or (3 if args.pc_type >= 3 else 16),
-              ew_eta0=args.ew_eta0)
+              ew_eta0=args.ew_eta0, guess=1 if args.guess == "ptilde" else 0)
     o32 = chns.SolverOpts.make(precision=1, **kw)
     o64 = chns.SolverOpts.make(precision=0, **kw)
     fields = {"v": slice(0, d), "p": slice(d, d + 1), "phi": slice(d + 1, d + 2), "mu": slice(d + 2, d + 3)}
     out = {"run": args.mesh, "elements": gm.E, "nodes": gm.N, "dof": dof, "hanging": gm.H,
            "mass0": chns.mass(gm, U0), "energy0": chns.energy(gm, prm, U0), "steps": []}
     Um, U64 = U0.clone(), U0.clone()
+    prev = {"m": None, "64": None}      # U^{k-1} of each trajectory (--guess ptilde)
+
+    def first_iterate(U, key):
+        """U^k with the pressure of U^{k-1}: the mid-point pressure continues the previous
+        step's (the Crank-Nicolson pressure alternates around it)."""
+        if args.guess != "ptilde":
+            return None
+        G = U.clone()
+        if prev[key] is not None:
+            G[:, d] = prev[key][:, d]
+        return G
+
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     for k in range(args.newton_steps):
+        Gm = first_iterate(Um, "m")
         ev[0].record()
-        Um_new, st = chns.newton_step(gm, prm, o32, Um, check=False)
+        Um_new, st = chns.newton_step(gm, prm, o32, Um, U_out=Gm, check=False)
         ev[1].record()
         torch.cuda.synchronize()
         ms = ev[0].elapsed_time(ev[1])
@@ -388,8 +401,9 @@ def run_trajectory(args):
             print(json.dumps(rec), flush=True)
             break
         if k < args.fp64_steps:
+            G64 = first_iterate(U64, "64")
             ev[2].record()
-            U64_new, s64 = chns.newton_step(gm, prm, o64, U64, check=False)
+            U64_new, s64 = chns.newton_step(gm, prm, o64, U64, U_out=G64, check=False)
             ev[3].record()
             torch.cuda.synchronize()
             rec["fp64_ms"] = ev[2].elapsed_time(ev[3])
@@ -398,8 +412,8 @@ def run_trajectory(args):
                 f: float((Um_new[:, sl] - U64_new[:, sl]).norm() / U64_new[:, sl].norm().clamp_min(1e-300))
                 for f, sl in fields.items()}
             rec["rel_err_mixed_vs_fp64"]["all"] = float((Um_new - U64_new).norm() / U64_new.norm())
-            U64 = U64_new
-        Um = Um_new
+            prev["64"], U64 = U64, U64_new
+        prev["m"], Um = Um, Um_new
         out["steps"].append(rec)
         print(json.dumps(rec), flush=True)
     E = [sum(out["energy0"])] + [sum(r["energy"]) for r in out["steps"]]
@@ -431,6 +445,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--max-krylov", type=int, default=5000)
+    ap.add_argument("--guess", choices=["old", "ptilde"], default="old",
+                    help="--run: first Newton iterate U^k, or U^k with the pressure of U^{k-1}")
     ap.add_argument("--ew-eta0", type=float, default=0.0,
                     help="--run: Eisenstat-Walker forcing from this first tolerance (0: fixed krylov_rtol)")
     ap.add_argument("--pc-type", type=int, default=None,

@@ -124,6 +124,13 @@ typedef struct {
                             carries the momentum imbalance before the time derivative has
                             responded), and the first Newton iteration is limited by the
                             nonlinearity rather than by the linear solve. */
+    int32_t guess;       /* first Newton iterate of chns_newton_step: 0 = U_old (U_inout is
+                            overwritten with it); 1 = U_inout as passed (the caller's guess,
+                            e.g. the pressure p^{k-1}, which continues the previous step's
+                            mid-point pressure: with p^0 = 0 the Crank-Nicolson pressure
+                            p^{k+1} = 2 p~ - p^k alternates around p~, so U_old misses it).
+                            The phi integral is still held at that of U_old; the pressure
+                            mean is that of the first iterate.  Other values: CHNS_EINVAL. */
 } chns_solver_opts;
 
 #define CHNS_HIST 32
@@ -224,7 +231,8 @@ chns_status chns_vjp(const chns_mesh* mesh, const chns_params* params, const dou
                      double* gCn, void* stream);
 
 /* One implicit time step (Section 3.4): solve R(U_old, U) = 0 by inexact Newton from
- * U^{0} = U_old (U_inout is overwritten with U_old first) with matrix-free GMRES.
+ * U^{0} = U_old (U_inout is overwritten with U_old first), or from U_inout as passed
+ * (opts->guess = 1), with matrix-free GMRES.  U_inout must not alias U_old.
  * With pin_pressure = 2, GMRES runs on J + u m_p^T / |Omega| (u = |diag J| on the
  * pressure rows, m_p the nodal masses): nonsingular, with the zero-mean-pressure
  * solution of J dU = -R.  U_old, U_inout: device, N * n_f doubles.  stats: host, may

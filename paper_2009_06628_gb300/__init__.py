@@ -45,13 +45,14 @@ class SolverOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("atol", ctypes.c_double), ("krylov_rtol", ctypes.c_double),
                 ("max_newton", ctypes.c_int32), ("max_krylov", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("pc_type", ctypes.c_int32), ("pc_degree", ctypes.c_int32),
-                ("ew_eta0", ctypes.c_double)]
+                ("ew_eta0", ctypes.c_double), ("guess", ctypes.c_int32)]
 
     @classmethod
     def make(cls, rtol=1e-9, atol=1e-14, krylov_rtol=1e-3, max_newton=20, max_krylov=2000, restart=60,
-             precision=1, pc_type=1, pc_degree=8, ew_eta0=0.0):
+             precision=1, pc_type=1, pc_degree=8, ew_eta0=0.0, guess=0):
         return cls(rtol=rtol, atol=atol, krylov_rtol=krylov_rtol, max_newton=max_newton, max_krylov=max_krylov,
-                   restart=restart, precision=precision, pc_type=pc_type, pc_degree=pc_degree, ew_eta0=ew_eta0)
+                   restart=restart, precision=precision, pc_type=pc_type, pc_degree=pc_degree, ew_eta0=ew_eta0,
+                   guess=guess)
 
 
 class Stats(ctypes.Structure):
@@ -241,6 +242,10 @@ def vjp(mesh, prm, U_old, U_lin, w, want_old=True, want_cn=True):
 
 
 def newton_step(mesh, prm, opts, U_old, U_out=None, check=True):
+    """One implicit step from U_old; with opts.guess = 1, U_out (required) holds the first
+    Newton iterate on entry."""
+    if opts.guess and U_out is None:
+        raise ValueError("opts.guess = 1 needs U_out holding the first iterate")
     U_out = torch.empty_like(U_old) if U_out is None else U_out
     st = Stats()
     code = load().chns_newton_step(mesh.handle, ctypes.byref(prm), ctypes.byref(opts), _ptr(U_old), _ptr(U_out),

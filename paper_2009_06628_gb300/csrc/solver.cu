@@ -1372,9 +1372,9 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
     if (o->restart < 1 || o->restart > MAXSC / 4 || o->max_krylov < 1 || o->max_newton < 0 ||
         (o->precision != 0 && o->precision != 1) || (o->pc_type < 0 || o->pc_type > 4) ||
         (o->pc_type >= 1 && (o->pc_degree < 2 || o->pc_degree > 200)) ||
-        !(o->ew_eta0 == 0.0 || (o->ew_eta0 > 0.0 && o->ew_eta0 < 1.0))) {
+        !(o->ew_eta0 == 0.0 || (o->ew_eta0 > 0.0 && o->ew_eta0 < 1.0)) || (o->guess != 0 && o->guess != 1)) {
         chns_set_error("bad solver options (restart in [1, 256], max_krylov >= 1, precision 0/1, pc_type 0..4, "
-                       "pc_degree in [2, 200], ew_eta0 0 or in (0, 1))");
+                       "pc_degree in [2, 200], ew_eta0 0 or in (0, 1), guess 0/1)");
         return CHNS_EINVAL;
     }
     if ((st = ensure_ws(m, o->restart)) != CHNS_OK) return st;
@@ -1398,7 +1398,7 @@ extern "C" chns_status chns_newton_step(const chns_mesh* mc, const chns_params* 
     S.reason = CHNS_OK;
 
     CHNS_CUDA(cudaMemsetAsync(m->d_flags, 0, sizeof(unsigned int), c.s));
-    { copy64_kernel<<<c.g, 256, 0, c.s>>>(U_old, U, c.n); chns_count_launches(1); }
+    if (o->guess == 0) { copy64_kernel<<<c.g, 256, 0, c.s>>>(U_old, U, c.n); chns_count_launches(1); }
     if (mixed) { to32_kernel<<<c.g, 256, 0, c.s>>>(U_old, ws->Uo32, c.n); chns_count_launches(1); }
     CHNS_CUDA(cudaGetLastError());
 

@@ -110,3 +110,11 @@ def test_struct_layouts_match_the_header(chns, tmp_path):
         assert int(out[cname]) == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert int(out[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)
+
+
+def test_guess_option_needs_a_first_iterate(chns):
+    """opts.guess = 1 starts Newton from U_out as passed, so the binding refuses the call
+    without one (on the host, before the library is entered)."""
+    import torch
+    with pytest.raises(ValueError):
+        chns.newton_step(None, None, chns.SolverOpts.make(guess=1), torch.zeros(4, 5, dtype=torch.float64))
